@@ -1,0 +1,29 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+The oracle source carries a few compile-time switches (OR_MUTANT = m) that each
+plant one plausible mistake: a dropped term, a wrong sign, a transposed
+operand, a wrong stencil or coefficient. Each mutant is built on the CPU and
+the pins that target it must fail, which shows the pins are sharp enough.
+"""
+import pytest
+
+import oracle_pins as P
+
+MUTANTS = {
+    1: ("feq: -u^2 term dropped", [P.check_feq_moments]),
+    2: ("feq: sign of v.u flipped", [P.check_feq_moments]),
+    3: ("CS: streams to x - c_k", [P.check_cs_streaming_direction]),
+    4: ("velocity components transposed", [P.check_set_ordering]),
+    5: ("WENO: mirrored third candidate", [P.check_weno_quadratic_exact]),
+    6: ("RK3: wrong second-stage weights", [P.check_fd_rk3_relaxation]),
+    7: ("WENO: downwind stencil for v > 0", [P.check_fd_linear_advection, P.check_fd_linear_modes]),
+    8: ("WENO: wrong beta_2 coefficient", [P.check_weno_beta]),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_mutant_is_caught(mutant):
+    what, checks = MUTANTS[mutant]
+    for check in checks:
+        with pytest.raises(AssertionError):
+            check(mutant)
