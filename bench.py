@@ -1,0 +1,362 @@
+"""Throughput of the CS and FD lattice Boltzmann hot path on GB300.
+
+One step = one pass of the whole path over the roofline workload, advanced
+together as one batch: a CS D2Q9 step on an 8192^2 lattice (collide + stream,
+one launch), an FD 16-velocity step on a 4096^2 lattice (three SSP-RK3 stage
+launches with WENO-5 and BGK), and the fused float64 observables (mass,
+momentum, Taylor-Green amplitude) of both lattices. Storage is FP32
+deviations; both states are far larger than L2 (2.4 GB and 3.2 GB), so
+nothing is flushed between steps.
+
+Metric: MLUPS (million lattice-node updates per second) over the workload,
+whole job (all ranks); per-kernel CUDA-event durations give the roofline
+fraction of the dominant kernel against the measured HBM copy bandwidth.
+
+--impl reference times the FP64 C oracle on the host cores instead (the
+paper publishes no implementation or timings), on bounded samples.
+Multi-GPU: replicas only (each rank advances its own copy; no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_workloads as wl  # noqa: E402
+
+CS_N = 8192
+FD_N = 4096
+FD_DT = 1e-5
+FD_TAU = 5e-4
+CS_TAU = 0.8 / math.sqrt(3.0)
+U0 = 0.01
+METRIC = "MLUPS & % HBM roofline, CS and FD; batched FP32 vs plain FP64; p50/p99"
+WORKLOAD = "roofline lattices: CS D2Q9 8192^2 + FD 16-velocity 4096^2, FP32 deviation storage, Taylor-Green"
+# algorithmic bytes per lattice update (FP32): CS reads and writes 9 values;
+# an FD step reads Q, 2Q, 2Q and writes Q, Q, Q values over its three stages.
+CS_BYTES_LU = 18 * 4
+FD_BYTES_LU = 8 * 16 * 4
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rates(budget_s: float = 12.0):
+    """Seconds per lattice update of the FP64 C oracle (single thread) on this
+    host: CS D2Q9 and FD 16-velocity, timed on bounded samples."""
+    import oracle
+    out = {}
+    n = 512
+    rho, ux, uy = wl.taylor_green(n, n, U0 * math.sqrt(3))
+    f = oracle.equilibrium(3, rho, ux, uy)
+    oracle.cs_run(f, CS_TAU, 1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s * 0.25:
+        f = oracle.cs_run(f, CS_TAU, 2)
+        steps += 2
+    out["cs"] = (time.perf_counter() - t0) / (steps * n * n)
+    out["cs_sample"] = f"CS D2Q9 {n}^2 x {steps} steps"
+    n = 128
+    rho, ux, uy = wl.taylor_green(n, n, U0)
+    f = oracle.equilibrium(4, rho, ux, uy)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s * 0.75:
+        f = oracle.fd_run(f, 1.0 / n, 2e-4, FD_TAU, 1)
+        steps += 1
+    out["fd"] = (time.perf_counter() - t0) / (steps * n * n)
+    out["fd_sample"] = f"FD 16-velocity {n}^2 x {steps} steps"
+    return out
+
+
+def cpu_value(rates):
+    cells = CS_N * CS_N + FD_N * FD_N
+    per_step = CS_N * CS_N * rates["cs"] + FD_N * FD_N * rates["fd"]
+    return cells / per_step / 1e6
+
+
+# ---------------------------------------------------------------- GPU arm
+def build_batch(torch, stream):
+    import paper_1904_02471_gb300 as pkg
+    specs = [pkg.make_spec("cs", 3, CS_N, CS_N, CS_TAU, 0.0, 0.0, "fp32"),
+             pkg.make_spec("fd", 4, FD_N, FD_N, FD_TAU, FD_DT, 0.0, "fp32")]
+    B = pkg.Batch(specs, stream=stream)
+    fields = []
+    for i, (n, U) in enumerate(((CS_N, U0 * math.sqrt(3)), (FD_N, U0))):
+        rho, ux, uy = wl.taylor_green(n, n, U)
+        pin = [torch.from_numpy(a).pin_memory().numpy() for a in (rho, ux, uy)]
+        fields.append(pin)
+        comp, px, py, norm = wl.probe_taylor_green(n, n)
+        B.set_probe(i, comp, px, py, norm)
+    return B, fields
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_1904_02471_gb300 as pkg  # noqa: F401
+    from paper_1904_02471_gb300 import build
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    rates = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rates = oracle_rates(args.cpu_budget)
+
+    stream = torch.cuda.Stream()
+    B, fields = build_batch(torch, stream)
+    for i in range(2):
+        B.init(i, *fields[i])
+    tune_report = B.tune(2)
+    groups = B.groups()
+    cap = args.warmup + args.steps + 8
+    for i in range(2):
+        B.record(i, 1, cap)
+    B.step_profiled(args.warmup)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = B.kernel_launches
+    w0 = time.perf_counter()
+    ms, total_ms = B.step_profiled(args.steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = B.kernel_launches - l0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_max = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    # check the run stayed finite and conserved mass (float64 sums)
+    ser = [B.series(i) for i in range(2)]
+    finite = all(s["nonfinite"] == 0 for sr in ser for s in sr)
+    drift = [abs(sr[-1]["mass"] - sr[0]["mass"]) / sr[0]["mass"] for sr in ser]
+
+    # e2e through the public API: host fields in (pinned), K steps, observables out
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for i in range(2):
+        B.init(i, *fields[i])
+    B.step(args.steps)
+    obs = [B.observables(i) for i in range(2)]
+    e_wall = time.perf_counter() - e0
+    assert all(o["nonfinite"] == 0 for o in obs)
+    h2d = sum(a.nbytes for fl in fields for a in fl) / args.steps
+    d2h = 2 * 48 / args.steps
+
+    peak, peak_kind = peaks()
+    gi = {(g["model"], g["q"]): k for k, g in enumerate(groups)}
+    gcs, gfd = gi[(0, 3)], gi[(1, 4)]
+    K = args.steps
+    cs_ms = ms[gcs][0] / K
+    fd_stage_ms = [ms[gfd][s] / K for s in range(3)]
+    fin_ms = (ms[gcs][3] + ms[gfd][3]) / K
+    cells = CS_N * CS_N + FD_N * FD_N
+    value = world * cells * K / (t_max / 1e3) / 1e6
+    cs_gbs = CS_N * CS_N * CS_BYTES_LU / (cs_ms / 1e3) / 1e9
+    fd_stage_avg = sum(fd_stage_ms) / 3
+    fd_gbs = FD_N * FD_N * FD_BYTES_LU / 3 / (fd_stage_avg / 1e3) / 1e9
+    traffic = committed_traffic()
+    rec = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (Taylor-Green initial state, seeded generators)",
+        "config": {
+            "workload": WORKLOAD,
+            "cs": {"lattice": [CS_N, CS_N], "tau_lu": CS_TAU, "velocities": 9},
+            "fd": {"lattice": [FD_N, FD_N], "tau_fd": FD_TAU, "dt_fd": FD_DT, "velocities": 16,
+                   "scheme": "WENO-5 + SSP-RK3, 3 stage launches"},
+            "observables": "fused float64 mass/momentum/amplitude every step",
+            "l2": "inputs larger than L2 (2.4 GB + 3.2 GB resident state), no flush",
+            "parallelism": f"replicas x{world}",
+            "tuning": tune_report.strip(),
+        },
+        "per_model": {
+            "cs": {"mlups": round(CS_N * CS_N / (cs_ms / 1e3) / 1e6, 1), "ms_per_step": round(cs_ms, 4),
+                   "gbs": round(cs_gbs, 1), "frac_hbm": round(cs_gbs / peak, 3), "bytes_per_lu": CS_BYTES_LU},
+            "fd": {"mlups": round(FD_N * FD_N / (sum(fd_stage_ms) / 1e3) / 1e6, 1),
+                   "ms_per_step": round(sum(fd_stage_ms), 4), "stage_ms": [round(x, 4) for x in fd_stage_ms],
+                   "gbs": round(fd_gbs, 1), "frac_hbm": round(fd_gbs / peak, 3), "bytes_per_lu": FD_BYTES_LU},
+            "finalize_ms_per_step": round(fin_ms, 4),
+        },
+        "roofline": {"kernel": "fd_stage_kernel<float,32,*> (FD RK stage, Q=16)", "bound": "hbm",
+                     "achieved": round(fd_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(fd_gbs / peak, 4), "peak_source": peak_kind,
+                     "traffic": traffic.get("fd_stage") if traffic else None,
+                     "algorithmic_bytes_per_launch": FD_N * FD_N * FD_BYTES_LU // 3},
+        "e2e": {"value": round(world * cells * K / e_wall / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "checks": {"finite": finite, "rel_mass_drift": [float(f"{d:.3e}") for d in drift],
+                   "host_wall_s": round(wall, 4)},
+    }
+    if rates is not None:
+        rec["cpu_baseline"] = {"value": round(cpu_value(rates), 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                               "sample": f"{rates['cs_sample']}; {rates['fd_sample']}; FP64 C oracle, one thread, "
+                                         "rates extrapolated per node update to the workload mix"}
+    B.close()
+    if dist:
+        dist.destroy_process_group()
+    return rec
+
+
+def committed_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_1904_02471_gb300 import build
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("source_digest") != build.kernel_digest():
+            return None
+        return d.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle  # noqa: F401
+    t_steps = []
+    rates = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_rates(args.cpu_budget / max(1, args.steps))
+        if s >= args.warmup:
+            t_steps.append(r)
+        rates = r
+    cs = statistics.median(r["cs"] for r in t_steps)
+    fd = statistics.median(r["fd"] for r in t_steps)
+    val = cpu_value({"cs": cs, "fd": fd})
+    per_step_s = CS_N * CS_N * cs + FD_N * FD_N * fd
+    sample = f"{rates['cs_sample']}; {rates['fd_sample']} per step; FP64 C oracle, one thread"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_s * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Taylor-Green initial state)",
+        "config": {"workload": WORKLOAD, "reference": "plain FP64 C oracle (no published implementation)"},
+        "cpu_baseline": {"value": round(val, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        rec = run_reference(args, rank, world)
+    else:
+        rec = run_gpu(args, rank, world)
+    if rank == 0 and rec is not None:
+        print(json.dumps(rec))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,311 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) isothermal lattice Boltzmann library.
+ *
+ * Two time-step updates for an ideal isothermal fluid on a periodic 2D
+ * lattice, after Negro et al., "Comparison between isothermal
+ * collision-streaming and finite-difference lattice Boltzmann models"
+ * (arXiv:1904.02471):
+ *
+ *  - LBM_CS, collision-streaming: Eq. (sc_evolution) with the D2Q9
+ *    Gauss-Hermite set (Sec. 2), dx = 1, dt = 1/sqrt(3), |v_ka| = sqrt(3);
+ *    collision and streaming fused into one pass.
+ *  - LBM_FD, finite-difference: Eq. (evolution) on a Gauss-Hermite product
+ *    set with q_per_axis roots per axis (Sec. 1-2), WENO-5 advection and
+ *    third-order TVD (SSP) Runge-Kutta time stepping (Sec. 2), with the BGK
+ *    term and the (rho, u) moments recomputed inside every stage.
+ *
+ * Units are the paper's: T = m = 1, so the sound speed is 1; f^eq is the
+ * second-order Hermite expansion Eq. (herfeq); rho and rho u follow
+ * Eq. (f_moments_discrete).
+ *
+ * Conventions shared by every call:
+ *  - Host field arrays are row-major [ny][nx] (x fastest), float64.
+ *  - Population arrays are [K][ny][nx], K = q_per_axis^2, population
+ *    k = ix + q*iy, ix / iy indexing the 1D Gauss-Hermite nodes in ascending
+ *    order (for D2Q9: nodes -sqrt3, 0, sqrt3; k = 4 is the rest velocity).
+ *  - Every call returns an int status (LBM_OK = 0 on success) unless stated;
+ *    lbm_strerror() names a code, lbm_last_error() gives the detail of the
+ *    last failure on the calling thread. No C++ exception or abort crosses
+ *    this interface. Host pointers are caller-owned and only read or written
+ *    during the call. Device memory is owned by the library.
+ *  - A context is not thread-safe: one thread at a time per context.
+ *    A server (lbm_server_*) is thread-safe.
+ *  - Work is enqueued on the context's CUDA stream; calls that return data to
+ *    host buffers synchronise that stream first.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* bad argument or inconsistent parameters */
+    LBM_ECFL = 2,        /* CFL = max|v_ka| dt/dx > 1 (Sec. 4.1) */
+    LBM_ESTIFF = 3,      /* FD with dt > tau: stiff collision term (Sec. 4.1) */
+    LBM_ENOMEM = 4,      /* device or host allocation failed, or over budget */
+    LBM_ECUDA = 5,       /* a CUDA runtime call failed (see lbm_last_error) */
+    LBM_ENOTREADY = 6,   /* result not available yet (lbm_poll) */
+    LBM_ETIMEOUT = 7,    /* a bounded wait ran out */
+    LBM_EBUSY = 8,       /* resource in use */
+    LBM_ENONFINITE = 9,  /* a non-finite mass or amplitude was observed */
+    LBM_ECANCELLED = 10, /* request cancelled before completion */
+    LBM_ENOTFOUND = 11   /* unknown ticket or index */
+};
+
+/* ---- model and storage selectors -------------------------------------- */
+enum { LBM_CS = 0, LBM_FD = 1 };
+/* LBM_FP64: populations stored and updated in float64.
+ * LBM_FP32_DEV: populations stored as float32 deviations g_k = f_k - w_k rho0
+ * from a uniform reference state, with float32 collision and advection;
+ * global sums (mass, momentum, amplitude) are accumulated in float64. */
+enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 };
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Observables of one state, Sec. 4.2-4.3 diagnostics.
+ * mass = sum rho, mom_x/mom_y = sum rho u, amp = norm * sum u_c px[x] py[y]
+ * (the probe set by lbm_set_probe; 0 if none). time = step * dt in the
+ * context's time unit. nonfinite != 0 if mass or amp is not finite. */
+typedef struct {
+    int64_t step;
+    double time;
+    double mass;
+    double mom_x;
+    double mom_y;
+    double amp;
+    int32_t nonfinite;
+    int32_t reserved;
+} lbm_obs;
+
+/* Parameters of a lattice. See lbm_create for their meaning. */
+typedef struct {
+    int model;        /* LBM_CS or LBM_FD */
+    int q_per_axis;   /* 3 for CS; 3, 4 or 5 for FD */
+    int nx, ny;       /* lattice nodes per axis, >= 1 */
+    int precision;    /* LBM_FP64 or LBM_FP32_DEV */
+    int reserved;
+    double tau;       /* CS: tau_LU; FD: tau_FD */
+    double dt;        /* time step (CS: 0 selects 1/sqrt(3)) */
+    double dx;        /* node spacing (CS: 0 selects 1; FD: 0 selects 1/nx) */
+    double rho0;      /* reference density of the FP32 deviation storage (0 selects 1) */
+} lbm_spec;
+
+/* ---- unit helpers (Sec. 3) ---------------------------------------------- */
+
+/* Kinematic viscosity of a model in its own units:
+ * CS, Eq. (nulu): nu_LU = tau_LU - dt/2; FD, Eq. (nu_fd): nu_FD = tau_FD
+ * (T = m = 1). Returns NaN for an unknown model. */
+double lbm_nu(int model, double tau, double dt);
+
+/* Eq. (nu-transfer): tau_LU = N tau_FD + sqrt(3)/6 for a CS lattice of N
+ * nodes along the reference length. */
+double lbm_tau_lu_from_fd(int n_lu, double tau_fd);
+
+/* Inverse of lbm_tau_lu_from_fd: tau_FD = (tau_LU - sqrt(3)/6) / N. */
+double lbm_tau_fd_from_lu(int n_lu, double tau_lu);
+
+/* Relaxation time in the usual lattice units (dt = 1, cs^2 = 1/3):
+ * tau* = tau_LU / dt_LU = sqrt(3) tau_LU. */
+double lbm_tau_star(double tau_lu);
+
+/* Largest FD time step allowed by CFL <= 1 and dt <= tau (Sec. 4.1):
+ * min(dx / max|v_ka|, tau). Returns NaN for q_per_axis outside 3..5. */
+double lbm_fd_max_dt(int q_per_axis, double dx, double tau);
+
+/* The velocity set used by the library (Sec. 1-2, Gauss-Hermite product
+ * set): writes K = q^2 entries to each of vx, vy, w (caller-owned).
+ * LBM_EINVAL for q outside 3..5. */
+int lbm_velocity_set(int q_per_axis, double* vx, double* vy, double* w);
+
+/* Least-squares fit of ln|a| = ln a0 - gamma t over the n samples with
+ * t >= t_skip (Sec. 4.2: nu_app from a numerical fit of Eq. (shear_sol);
+ * Sec. 4.3: of Eq. (taylor)). Writes gamma and a0. LBM_EINVAL if fewer than
+ * two samples qualify. */
+int lbm_fit_decay(const double* t, const double* a, int64_t n, double t_skip, double* gamma,
+                  double* a0);
+
+/* ---- a single lattice ---------------------------------------------------- */
+
+/* Create a lattice context (Sec. 2 models, Sec. 3 units).
+ *  model, q_per_axis: LBM_CS with q = 3 (D2Q9), or LBM_FD with q in 3..5.
+ *  nx, ny: periodic lattice size, each >= 1, nx*ny*K < 2^40.
+ *  tau: relaxation time in the model's units (CS tau_LU > dt/2; FD tau_FD > 0).
+ *  dt, dx: CS requires dx/dt = sqrt(3) (0, 0 select dx = 1, dt = 1/sqrt(3));
+ *      FD dx = 0 selects 1/nx (unit domain), dt must be > 0.
+ *  precision: LBM_FP64 or LBM_FP32_DEV. rho0: reference density of the
+ *      deviation storage (0 selects 1; ignored for LBM_FP64).
+ *  cuda_stream: a cudaStream_t to enqueue work on, or NULL for a stream the
+ *      library creates (the legacy default stream is never used).
+ * Errors: LBM_EINVAL (bad sizes, model/q pair, tau <= dt/2 for CS, dx/dt),
+ *  LBM_ECFL (max|v_ka| dt/dx > 1), LBM_ESTIFF (FD dt > tau), LBM_ENOMEM,
+ *  LBM_ECUDA. On error *out is NULL. The state is zero until lbm_init. */
+int lbm_create(lbm_ctx** out, int model, int q_per_axis, int nx, int ny, double tau, double dt,
+               double dx, int precision, double rho0, void* cuda_stream);
+
+/* Same as lbm_create with the parameters in a struct. */
+int lbm_create_spec(lbm_ctx** out, const lbm_spec* spec, void* cuda_stream);
+
+/* Release all device memory of the context (after finishing its stream).
+ * NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Parameters actually in use (defaults resolved). */
+int lbm_get_spec(const lbm_ctx* ctx, lbm_spec* out);
+
+/* WENO-5 smoothness regulariser epsilon (FD only, default 1e-6; Sec. 2 cites
+ * Jiang-Shu WENO-5 without printing it). FP32 storage accepts [1e-8, 1e9],
+ * FP64 [1e-60, 1e60]; LBM_EINVAL otherwise or for a CS context. */
+int lbm_set_weno_eps(lbm_ctx* ctx, double eps);
+
+/* Initialise f = f^eq(rho, u) (Eq. herfeq) from host fields rho, ux, uy,
+ * each [ny][nx]; rho must be > 0 and finite (LBM_EINVAL otherwise). The step
+ * counter restarts at 0. The paper does not state its initial populations;
+ * the equilibrium is the reading used here. */
+int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/* Load an arbitrary state: f is [K][ny][nx] full populations (for
+ * LBM_FP32_DEV they are stored as float32(f - w_k rho0)). The step counter
+ * is kept. */
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Enqueue n >= 0 time steps on the context stream and return. One step is
+ * one application of Eq. (sc_evolution) (CS) or one three-stage RK step (FD). */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Wait for all enqueued work. Returns LBM_ECUDA if a kernel failed. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Number of steps completed or enqueued since lbm_init. */
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+
+/* Synchronous readout of rho, ux, uy (host [ny][nx] each, caller-owned) of
+ * the current state, Eq. (f_moments_discrete). */
+int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Synchronous readout of the current populations f[K][ny][nx] (host),
+ * as full f in float64. For CS this is the pre-collision state f(x, t) of
+ * Eq. (sc_evolution) (the kernels store another phase internally). */
+int lbm_populations(lbm_ctx* ctx, double* f);
+
+/* Synchronous readout of a window of the current populations: f[K][wy][wx]
+ * (host) receives the full f at nodes (x0 + i) mod nx, (y0 + j) mod ny for
+ * 0 <= i < wx, 0 <= j < wy. Requires 0 <= x0 < nx, 0 <= y0 < ny,
+ * 1 <= wx <= nx, 1 <= wy <= ny (LBM_EINVAL otherwise). Same phase and
+ * precision conventions as lbm_populations. */
+int lbm_populations_region(lbm_ctx* ctx, int x0, int y0, int wx, int wy, double* f);
+
+/* Amplitude probe for the observables: A = norm * sum_{x,y} u_comp px[x] py[y],
+ * comp 0 = u_x, 1 = u_y; px has nx entries and py ny entries (host, copied).
+ * Shear wave (Sec. 4.2): comp 1, px = sin(kx), py = 1, norm = 2/(nx ny).
+ * Taylor-Green (Sec. 4.3): comp 0, px = sin(kx), py = cos(ky), norm = 4/(nx ny). */
+int lbm_set_probe(lbm_ctx* ctx, int comp, const double* px, const double* py, double norm);
+
+/* Synchronous observables of the current state (float64 global sums). */
+int lbm_observables(lbm_ctx* ctx, lbm_obs* out);
+
+/* Record the observables of every state whose step index is a multiple of
+ * `every` (0 switches recording off) during later lbm_step calls, fused into
+ * the step kernels, into a device series of `capacity` records. Resets the
+ * series. */
+int lbm_record(lbm_ctx* ctx, int64_t every, int64_t capacity);
+
+/* Copy up to cap recorded observables (oldest first) to out; *count receives
+ * the number recorded so far (capped at the capacity). Synchronous. */
+int lbm_series(lbm_ctx* ctx, lbm_obs* out, int64_t cap, int64_t* count);
+
+/* Checkpoint: lbm_checkpoint_size bytes hold the parameters, the step
+ * counter and the raw state, so that lbm_load + lbm_step continues
+ * bit-identically. lbm_load needs a context with the same spec. */
+size_t lbm_checkpoint_size(const lbm_ctx* ctx);
+int lbm_save(lbm_ctx* ctx, void* host_buf, size_t size);
+int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t size);
+
+/* Device view of the storage, for zero-copy use (e.g. as torch tensors).
+ * base points to plane 0 of the buffer that holds the current state;
+ * element (k, y, x) is at base + k*plane + y*pitch + x, in float64
+ * (LBM_FP64) or float32 deviations (LBM_FP32_DEV). For CS the stored phase
+ * is the post-collision state shifted: f_k(x, t) = stored_k(x - c_k).
+ * Valid until the next lbm_step. */
+typedef struct {
+    void* base;
+    int64_t plane;
+    int32_t pitch;
+    int32_t elem_bytes;
+    int32_t cs_pull_phase;
+    int32_t reserved;
+} lbm_view;
+int lbm_device_view(lbm_ctx* ctx, lbm_view* out);
+
+/* ---- many lattices in one launch ------------------------------------------ */
+
+/* A batch advances n independent lattices (any mix of CS/FD, sizes,
+ * precisions, tau) together: each step is one persistent launch per
+ * (model, q, precision) group over a work list of (lattice, tile) items,
+ * and chunks of steps are replayed from a captured CUDA graph. Every
+ * lattice in a batch computes exactly what it computes alone. */
+typedef struct lbm_batch lbm_batch;
+
+int lbm_batch_create(lbm_batch** out, const lbm_spec* specs, int n, void* cuda_stream);
+void lbm_batch_destroy(lbm_batch* b);
+int lbm_batch_size(const lbm_batch* b);
+/* Initialise lattice i from host fields (as lbm_init). */
+int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy);
+/* Steps still to run for lattice i; lattices with 0 left are skipped by
+ * later lbm_batch_step calls (default: unlimited). */
+int lbm_batch_set_budget(lbm_batch* b, int i, int64_t steps);
+/* Enqueue n steps for every lattice that has budget left. */
+int lbm_batch_step(lbm_batch* b, int64_t n);
+int lbm_batch_sync(lbm_batch* b);
+int64_t lbm_batch_steps_done(const lbm_batch* b, int i);
+int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy);
+int lbm_batch_populations(lbm_batch* b, int i, double* f);
+int lbm_batch_populations_region(lbm_batch* b, int i, int x0, int y0, int wx, int wy, double* f);
+int lbm_batch_set_probe(lbm_batch* b, int i, int comp, const double* px, const double* py,
+                        double norm);
+int lbm_batch_observables(lbm_batch* b, int i, lbm_obs* out);
+
+/* Observables recording for lattice i of a batch (as lbm_record / lbm_series). */
+int lbm_batch_record(lbm_batch* b, int i, int64_t every, int64_t capacity);
+int lbm_batch_series(lbm_batch* b, int i, lbm_obs* out, int64_t cap, int64_t* count);
+
+/* The groups of a batch (one per model, q, precision) in launch order:
+ * fills up to cap entries of model/q/precision (each may be NULL) and
+ * returns the number of groups (-1 for a NULL batch). */
+int lbm_batch_groups(lbm_batch* b, int* model, int* q, int* precision, int cap);
+
+/* Measurement: n steps launched one kernel at a time with CUDA events around
+ * every kernel (no graph). ms[g*4 + k] (cap entries, caller-owned) receives
+ * the summed device time of group g's kernels of kind k: 0..2 = CS step or FD
+ * stages 1..3, 3 = observables finalisation; *total_ms the span of all n
+ * steps. Computes exactly what lbm_batch_step(n) computes. Synchronous. */
+int lbm_batch_step_profiled(lbm_batch* b, int64_t n, double* ms, int cap, double* total_ms);
+
+/* Number of kernels the library has enqueued for this batch / context so
+ * far (nodes of replayed graphs included). */
+int64_t lbm_batch_kernel_launches(const lbm_batch* b);
+int64_t lbm_kernel_launches(const lbm_ctx* ctx);
+
+/* Autotuner: times the candidate tile shapes and grid sizes of every group
+ * of the batch on its current state (state is saved and restored) and keeps
+ * the fastest; results are cached per (model, q, precision, size class).
+ * trial_steps > 0 steps per candidate. Writes a one-line summary into
+ * report (may be NULL) of report_len bytes. */
+int lbm_batch_tune(lbm_batch* b, int trial_steps, char* report, size_t report_len);
+
+/* ---- errors ---------------------------------------------------------------- */
+const char* lbm_strerror(int code);
+const char* lbm_last_error(void);
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,117 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol include/lbm.h
+declares, and its host-only logic (unit helpers, velocity sets, parameter
+validation, decay fit) is right. No GPU compute is called here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle_pins as P
+from paper_1904_02471_gb300 import lbm
+import paper_1904_02471_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_02471_gb300 import build
+    build.build()
+
+
+def test_every_declared_symbol_is_exported():
+    L = lbm.lib()
+    declared = _declared()
+    assert len(declared) > 30
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding covers every declared entry point
+    assert declared <= set(lbm.exported_names()) | set(), sorted(declared - set(lbm.exported_names()))
+
+
+def test_version_and_errors():
+    assert "sm_103a" in lbm.lib().lbm_version().decode()
+    for code in range(12):
+        assert lbm.strerror(code) != "unknown error"
+
+
+def test_velocity_sets_match_numpy_gauss_hermite():
+    from numpy.polynomial.hermite_e import hermegauss
+    for q in (3, 4, 5):
+        vx, vy, w = pkg.lbm_velocity_set(q)
+        x, wr = hermegauss(q)
+        wr = wr / wr.sum()
+        for k in range(q * q):
+            assert abs(vx[k] - x[k % q]) < 1e-14 and abs(vy[k] - x[k // q]) < 1e-14
+            assert abs(w[k] - wr[k % q] * wr[k // q]) < 1e-15
+
+
+def test_unit_helpers_against_printed_values():
+    g = P._golden("paper_values.json")
+    t = g["tau_lu_tables"]
+    for n, printed in t["rows"]:
+        assert P._trunc(pkg.lbm_tau_lu_from_fd(n, t["tau_fd"]), t["digits"]) == printed
+        assert abs(pkg.lbm_tau_fd_from_lu(n, pkg.lbm_tau_lu_from_fd(n, t["tau_fd"])) - t["tau_fd"]) < 1e-15
+        # Eq. (nulu) with the CS dt: nu_LU = N nu_FD
+        tl = pkg.lbm_tau_lu_from_fd(n, t["tau_fd"])
+        assert abs(pkg.lbm_nu(lbm.LBM_CS, tl, 1 / math.sqrt(3)) - n * t["tau_fd"]) < 1e-14
+    s = g["tau_lu_shock"]
+    for tau_fd, printed, digits in s["rows"]:
+        assert P._trunc(pkg.lbm_tau_lu_from_fd(s["n"], tau_fd), digits) == printed
+    assert pkg.lbm_nu(lbm.LBM_FD, 5e-4, 1.0) == 5e-4
+    assert abs(pkg.lbm_tau_star(0.8 / math.sqrt(3)) - 0.8) < 1e-15
+    # CFL / stiffness bound (Sec. 4.1)
+    assert abs(pkg.lbm_fd_max_dt(3, 1 / 2048, 1e-3) - 1 / (2048 * math.sqrt(3))) < 1e-18
+    assert pkg.lbm_fd_max_dt(4, 1 / 256, 1e-5) == 1e-5
+
+
+def test_fit_decay():
+    t = np.linspace(0, 10, 50)
+    a = 0.3 * np.exp(-0.25 * t)
+    g, a0 = pkg.lbm_fit_decay(t, a, 1.0)
+    assert abs(g - 0.25) < 1e-12 and abs(a0 - 0.3) < 1e-12
+    with pytest.raises(lbm.LbmError):
+        pkg.lbm_fit_decay(t[:1], a[:1])
+
+
+@pytest.mark.parametrize("args,code", [
+    (("cs", 3, 8, 8, 0.2), lbm.LBM_EINVAL),                       # tau_LU <= dt/2
+    (("cs", 4, 8, 8, 0.5), lbm.LBM_EINVAL),                       # CS is D2Q9 only
+    (("cs", 3, 8, 8, 0.5, 0.5, 1.0), lbm.LBM_EINVAL),             # dx/dt != sqrt(3)
+    (("fd", 4, 32, 32, 1e-2, 1.5e-2), lbm.LBM_ECFL),              # 2.33 * 0.015 * 32 > 1
+    (("fd", 4, 32, 32, 1e-4, 1e-3), lbm.LBM_ESTIFF),              # dt > tau
+    (("fd", 6, 8, 8, 1.0, 1e-3), lbm.LBM_EINVAL),                 # no such set
+    (("fd", 4, 0, 8, 1.0, 1e-3), lbm.LBM_EINVAL),                 # empty lattice
+    (("fd", 4, 8, 8, -1.0, 1e-3), lbm.LBM_EINVAL),                # negative tau
+    (("fd", 4, 8, 8, 1.0, 0.0), lbm.LBM_EINVAL),                  # dt = 0
+])
+def test_create_validation(args, code):
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Lattice(*args)
+    assert ei.value.code == code
+
+
+def test_batch_validation_names_the_lattice():
+    specs = [pkg.make_spec("cs", 3, 8, 8, 0.5), pkg.make_spec("fd", 4, 32, 32, 1e-4, 1e-3)]
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Batch(specs)
+    assert ei.value.code == lbm.LBM_ESTIFF and "lattice 1" in str(ei.value)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        lbm.lib()
