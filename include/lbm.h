@@ -287,6 +287,14 @@ int lbm_batch_groups(lbm_batch* b, int* model, int* q, int* precision, int cap);
  * steps. Computes exactly what lbm_batch_step(n) computes. Synchronous. */
 int lbm_batch_step_profiled(lbm_batch* b, int64_t n, double* ms, int cap, double* total_ms);
 
+/* Kernel configuration of group `group` of a batch (lbm_batch_groups order):
+ * tile variant 0 .. lbm_n_tiles(model)-1 and persistent grid size (0 picks
+ * one CTA set per SM from occupancy). Every variant computes bit-identical
+ * results; only speed differs. lbm_config does the same for a context. */
+int lbm_batch_config(lbm_batch* b, int group, int tile, int grid);
+int lbm_config(lbm_ctx* ctx, int tile, int grid);
+int lbm_n_tiles(int model);
+
 /* Number of kernels the library has enqueued for this batch / context so
  * far (nodes of replayed graphs included). */
 int64_t lbm_batch_kernel_launches(const lbm_batch* b);

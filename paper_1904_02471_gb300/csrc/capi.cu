@@ -415,6 +415,24 @@ int lbm_batch_step_profiled(lbm_batch* b, int64_t n, double* ms, int cap, double
     GUARD_END
 }
 
+int lbm_batch_config(lbm_batch* b, int group, int tile, int grid) {
+    GUARD_BEGIN
+    if (!b) return LBM_EINVAL;
+    return b->e.set_group_config(group, tile, grid);
+    GUARD_END
+}
+
+int lbm_config(lbm_ctx* c, int tile, int grid) {
+    GUARD_BEGIN
+    if (!c) return LBM_EINVAL;
+    return c->e.set_group_config(0, tile, grid);
+    GUARD_END
+}
+
+int lbm_n_tiles(int model) {
+    return model == LBM_CS ? (int)lbm::CS_NTILES : (model == LBM_FD ? (int)lbm::FD_NTILES : -1);
+}
+
 int64_t lbm_batch_kernel_launches(const lbm_batch* b) {
     return b ? const_cast<lbm_batch*>(b)->e.kernel_launches() : -1;
 }

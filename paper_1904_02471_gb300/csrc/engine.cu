@@ -2,9 +2,12 @@
 //
 // Layout in HBM: each lattice owns one allocation holding its 2 (CS) or 3
 // (FD) state buffers; a buffer is K population planes [ny][pitch], x fastest,
-// pitch = nx rounded up to 32 elements (128-byte rows for FP32), plane
-// stride = pitch * ny. Tile partials, descriptors and probe tables are small
-// side allocations.
+// pitch = nx + 8 rounded up to 32 elements (128-byte rows for FP32), plane
+// stride = pitch * ny. Element (0, 0) of a buffer sits HEAD = 4 elements into
+// its slot and each slot ends with TAIL = 1024 spare elements, so a row
+// segment [x0 - 4, x0 + W + 4) read by the bulk-copy kernels (W <= 256) is
+// always 16-byte aligned and inside the allocation. Tile partials,
+// descriptors and probe tables are small side allocations.
 #include "engine.h"
 
 #include <algorithm>
@@ -154,7 +157,7 @@ int Engine::create(const lbm_spec* specs, int n, void* stream) {
         const lbm_spec& s = L.spec;
         L.K = s.q_per_axis * s.q_per_axis;
         L.elem = s.precision == LBM_FP64 ? 8 : 4;
-        L.pitch = (s.nx + 31) / 32 * 32;
+        L.pitch = (s.nx + 8 + 31) / 32 * 32;
         L.plane = (long long)L.pitch * s.ny;
         L.nbuf = s.model == LBM_CS ? 2 : 3;
         L.rho0s = s.precision == LBM_FP64 ? 0.0 : s.rho0;
@@ -168,8 +171,8 @@ int Engine::create(const lbm_spec* specs, int n, void* stream) {
         cudaError_t e = cudaMalloc(&L.mem, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
         CK(cudaMemsetAsync(L.mem, 0, bytes, stream_));
-        const size_t bbytes = (size_t)L.K * L.plane * L.elem;
-        for (int b = 0; b < L.nbuf; ++b) L.buf[b] = static_cast<char*>(L.mem) + b * bbytes;
+        for (int b = 0; b < L.nbuf; ++b)
+            L.buf[b] = static_cast<char*>(L.mem) + (b * L.buf_stride() + Lattice::HEAD) * L.elem;
         L.part_blocks = 1024;
         CK(cudaMalloc(&L.d_part, sizeof(double) * NOBS * L.part_blocks));
         CK(cudaMalloc(&L.d_snap, sizeof(double) * NOBS));
@@ -256,7 +259,7 @@ int Engine::upload_group(int gi) {
         const int cap = std::max(nm, 1);
         CK(cudaMalloc(&g.d_desc, sizeof(LatDesc) * cap));
         CK(cudaMalloc(&g.d_item_begin, sizeof(int) * cap));
-        CK(cudaMalloc(&g.d_hdr, sizeof(int) * 2));
+        CK(cudaMalloc(&g.d_hdr, sizeof(int) * 4));
         g.cap_lat = cap;
         invalidate_graph();
     }
@@ -285,7 +288,7 @@ int Engine::upload_group(int gi) {
     std::vector<LatDesc> descs;
     for (int m = 0; m < nm; ++m)
         descs.push_back(make_desc(lat[g.members[m]], g, begins[m], g.d_partials + (long long)begins[m] * NOBS));
-    const int hdr[2] = {nm, (int)items};
+    const int hdr[4] = {nm, (int)items, 0, 0};
     if (nm) {
         CK(cudaMemcpyAsync(g.d_desc, descs.data(), sizeof(LatDesc) * nm, cudaMemcpyHostToDevice, stream_));
         CK(cudaMemcpyAsync(g.d_item_begin, begins.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, stream_));
@@ -306,9 +309,13 @@ int Engine::upload_all() {
 }
 
 int Engine::set_group_config(int gi, int tile, int grid) {
-    if (gi < 0 || gi >= (int)groups.size()) return LBM_EINVAL;
+    if (gi < 0 || gi >= (int)groups.size()) { set_error("no such group"); return LBM_EINVAL; }
     Group& g = groups[gi];
-    if (tile < 0 || tile >= (g.model == LBM_CS ? (int)CS_NTILES : (int)FD_NTILES)) return LBM_EINVAL;
+    if (tile < 0 || tile >= (g.model == LBM_CS ? (int)CS_NTILES : (int)FD_NTILES) || grid < 0) {
+        set_error("no such tile variant");
+        return LBM_EINVAL;
+    }
+    CK(cudaStreamSynchronize(stream_));
     g.tile = tile;
     g.grid = 0;
     int rc = upload_group(gi);
@@ -480,6 +487,27 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
 int Engine::sync() {
     CK(cudaStreamSynchronize(stream_));
     CK(cudaGetLastError());
+    return check_device_errors();
+}
+
+// Error words the kernels raise instead of hanging (bounded waits that ran
+// out); read and cleared here.
+int Engine::check_device_errors() {
+    int bad = 0;
+    for (auto& g : groups) {
+        if (!g.d_hdr) continue;
+        int h[4];
+        CK(cudaMemcpy(h, g.d_hdr, sizeof h, cudaMemcpyDeviceToHost));
+        if (h[2] != 0) {
+            bad |= h[2];
+            const int zero = 0;
+            CK(cudaMemcpy(g.d_hdr + 2, &zero, sizeof zero, cudaMemcpyHostToDevice));
+        }
+    }
+    if (bad) {
+        set_error("a device-side wait ran out of time (bulk-copy pipeline); results of that step are invalid");
+        return LBM_ETIMEOUT;
+    }
     return LBM_OK;
 }
 

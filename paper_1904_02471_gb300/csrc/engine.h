@@ -51,7 +51,11 @@ struct Lattice {
     int group = -1;
     int slot = -1;
     bool active = true;      // member of its group's work list
-    size_t state_bytes() const { return (size_t)nbuf * K * plane * elem; }
+    // buffer b starts HEAD elements into its slot of the allocation; slots are
+    // K * plane + TAIL elements (see engine.cu for why)
+    static constexpr long long HEAD = 4, TAIL = 1024;
+    long long buf_stride() const { return (long long)K * plane + TAIL; }
+    size_t state_bytes() const { return (size_t)nbuf * buf_stride() * elem; }
 };
 
 struct Group {
@@ -97,6 +101,7 @@ class Engine {
     int step_profiled(long long n, double* ms, int cap, double* total_ms);
     long long kernel_launches() const { return launches_; }
     int sync();
+    int check_device_errors();
     int moments(int i, double* rho, double* ux, double* uy);
     int populations(int i, double* f);
     int populations_region(int i, int x0, int y0, int wx, int wy, double* f);

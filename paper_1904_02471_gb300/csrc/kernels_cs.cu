@@ -17,6 +17,7 @@
 // stored equilibrium is w_k [ (rho - rho0) + rho (xi + (xi^2 - u^2)/2) ],
 // xi = v_k . u, i.e. Eq. (herfeq) minus w_k rho0 (Sec. 2).
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace lbm {
 
@@ -100,10 +101,197 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised variant. A work item is W columns x RB rows of one
+// lattice. Warp 0 (one lane) streams, for every output row y, the nine
+// population row segments it gathers from (rows y - c_ky) into a ring of S
+// shared-memory slots with 1D bulk asynchronous copies; each slot's mbarrier
+// counts the bytes in. Warps 1..W/32 take one node per thread from the slot,
+// collide, store, and release the slot. A segment covers [x0 - 4, x0 + W + 4):
+// 16-byte aligned, inside the allocation (4 elements of padding precede x = 0
+// and every buffer has a tail pad), and it contains the x-1 / x+1 neighbours;
+// only the periodic wrap at x = 0 / nx - 1 is read from global memory.
+// All waits are bounded; a timeout sets hdr[2] and the block finishes
+// without waiting again.
+template <typename T, int W, int RB, int S>
+__host__ __device__ constexpr size_t cs_bulk_smem() {
+    return (size_t)S * 9 * (W + 8) * sizeof(T) + 2 * S * sizeof(uint64_t) + (W / 32) * NOBS * sizeof(double);
+}
+
+template <typename T, int W, int RB, int S>
+__global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
+    constexpr int NCW = W / 32;
+    constexpr int SEG = W + 8;
+    constexpr unsigned SEG_BYTES = SEG * sizeof(T);
+    constexpr unsigned SLOT_BYTES = 9 * SEG_BYTES;
+    extern __shared__ __align__(128) unsigned char sm[];
+    T* ring = reinterpret_cast<T*>(sm);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * SLOT_BYTES);
+    uint64_t* empty = full + S;
+    double* red = reinterpret_cast<double*>(empty + S);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int n_lat = g.hdr[0];
+    const int total = g.hdr[1];
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane != 0) return;
+        unsigned it = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < total && ok; item += gridDim.x) {
+            const int li = find_lattice(g.item_begin, n_lat, item);
+            const LatDesc* dp = g.desc + li;
+            if ((long long)j >= dp->remaining) continue;
+            const int ny = dp->ny, pitch = dp->pitch;
+            const long long plane = dp->plane;
+            const int local = item - dp->item_begin;
+            const int bx = local % dp->tiles_x, by = local / dp->tiles_x;
+            const int x0 = bx * W, y0 = by * RB;
+            const int y1 = min(y0 + RB, ny);
+            const T* in = static_cast<const T*>(dp->buf[dp->cur ^ (j & 1)]);
+            for (int y = y0; y < y1; ++y, ++it) {
+                const int s = it % S;
+                if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
+                const int ym = (y == 0) ? ny - 1 : y - 1;
+                const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int cy = c3_of(k / 3);
+                    const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                    bulk_g2s(ring + ((size_t)s * 9 + k) * SEG, in + k * plane + (long long)sy * pitch + x0 - 4, SEG_BYTES,
+                             &full[s]);
+                }
+            }
+        }
+        if (!ok) {
+            atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
+            // let the copies already issued land before the block exits
+            const unsigned first = it > (unsigned)S ? it - S : 0;
+            for (unsigned q = first; q < it; ++q) mbar_wait(&full[q % S], (q / S) & 1);
+        }
+        return;
+    }
+
+    // ---------------- consumers: one node per thread per row
+    const int ctid = threadIdx.x - 32;
+    unsigned it = 0;
+    bool dead = false;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int li = find_lattice(g.item_begin, n_lat, item);
+        const LatDesc* dp = g.desc + li;
+        if ((long long)j >= dp->remaining) continue;
+        const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
+        const long long plane = dp->plane;
+        const int local = item - dp->item_begin;
+        const int bx = local % dp->tiles_x, by = local / dp->tiles_x;
+        const int x0 = bx * W, y0 = by * RB;
+        const int y1 = min(y0 + RB, ny);
+        const int cur = dp->cur ^ (j & 1);
+        const T* __restrict__ in = static_cast<const T*>(dp->buf[cur]);
+        T* __restrict__ out = static_cast<T*>(dp->buf[cur ^ 1]);
+        const T omega = (T)dp->omega;
+        const T r0 = (T)dp->rho0;
+        const bool obs = observe_now(*dp, j);
+        const int pc = dp->probe_comp;
+        const int x = x0 + ctid;
+        const bool xin = x < nx;
+        T acc[NOBS] = {T(0), T(0), T(0), T(0)};
+        T pxv = T(0);
+        if (obs && pc >= 0 && xin) {
+            if constexpr (sizeof(T) == 4) pxv = dp->probe_pxf[x]; else pxv = (T)dp->probe_px[x];
+        }
+        for (int y = y0; y < y1; ++y, ++it) {
+            const int s = it % S;
+            if (!dead && !mbar_wait(&full[s], (it / S) & 1)) {
+                dead = true;
+                atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
+            }
+            if (!dead && xin) {
+                const T* slot = ring + (size_t)s * 9 * SEG;
+                const int ym = (y == 0) ? ny - 1 : y - 1;
+                const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+                T f[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+                    f[k] = slot[k * SEG + ctid + 4 - cx];
+                    if ((cx == 1 && x == 0) || (cx == -1 && x == nx - 1)) {
+                        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                        f[k] = in[k * plane + (long long)sy * pitch + (cx == 1 ? nx - 1 : 0)];
+                    }
+                }
+                T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    dr += f[k];
+                    if (vx_of<3>(k) != 0.0) jx += f[k] * (T)vx_of<3>(k);
+                    if (vy_of<3>(k) != 0.0) jy += f[k] * (T)vy_of<3>(k);
+                }
+                const T rho = r0 + dr;
+                const T inv = T(1) / rho;
+                const T ux = jx * inv, uy = jy * inv;
+                const T usq = ux * ux + uy * uy;
+                const long long row0 = (long long)y * pitch + x;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
+                    const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                    __stcs(out + k * plane + row0, f[k] - omega * (f[k] - geq));
+                }
+                if (obs) {
+                    acc[0] += dr;
+                    acc[1] += jx;
+                    acc[2] += jy;
+                    if (pc >= 0) {
+                        T pyv;
+                        if constexpr (sizeof(T) == 4) pyv = dp->probe_pyf[y]; else pyv = (T)dp->probe_py[y];
+                        acc[3] += (pc == 0 ? ux : uy) * pxv * pyv;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && !dead) mbar_arrive(&empty[s]);
+        }
+        if (obs) {
+            T r[NOBS];
+#pragma unroll
+            for (int q = 0; q < NOBS; ++q) {
+                T v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                r[q] = v;
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < NOBS; ++q) red[(warp - 1) * NOBS + q] = (double)r[q];
+            named_sync(1, W);
+            if (ctid < NOBS) {
+                double t = 0.0;
+                for (int w = 0; w < NCW; ++w) t += red[w * NOBS + ctid];
+                dp->partials[(long long)local * NOBS + ctid] = t;
+            }
+            named_sync(1, W);
+        }
+    }
+}
+
 int cs_tile_tx(int v) {
     switch (v) {
-        case CS_T128x1: case CS_T128x2: return 128;
-        case CS_T256x1: case CS_T256x2: return 256;
+        case CS_T128x1: case CS_T128x2: case CS_B128x32: return 128;
+        case CS_T256x1: case CS_T256x2: case CS_B256x32: return 256;
         case CS_T64x4: return 64;
     }
     return 0;
@@ -113,6 +301,7 @@ int cs_tile_ty(int v) {
         case CS_T128x1: case CS_T256x1: return 1;
         case CS_T128x2: case CS_T256x2: return 2;
         case CS_T64x4: return 4;
+        case CS_B256x32: case CS_B128x32: return 32;
     }
     return 0;
 }
@@ -125,23 +314,60 @@ static const void* cs_kernel_ptr(int tile) {
         case CS_T256x1: return (const void*)cs_step_kernel<T, 256, 1>;
         case CS_T256x2: return (const void*)cs_step_kernel<T, 256, 2>;
         case CS_T64x4: return (const void*)cs_step_kernel<T, 64, 4>;
+        case CS_B256x32: return (const void*)cs_bulk_kernel<T, 256, 32, 4>;
+        case CS_B128x32: return (const void*)cs_bulk_kernel<T, 128, 32, 6>;
     }
     return nullptr;
 }
 
+template <typename T>
+static size_t cs_smem(int tile) {
+    switch (tile) {
+        case CS_B256x32: return cs_bulk_smem<T, 256, 32, 4>();
+        case CS_B128x32: return cs_bulk_smem<T, 128, 32, 6>();
+    }
+    return 0;
+}
+
+static bool cs_is_bulk(int tile) { return tile == CS_B256x32 || tile == CS_B128x32; }
+
+static const void* cs_fn(int precision, int tile) {
+    return precision == LBM_FP64 ? cs_kernel_ptr<double>(tile) : cs_kernel_ptr<float>(tile);
+}
+static size_t cs_bytes(int precision, int tile) {
+    return precision == LBM_FP64 ? cs_smem<double>(tile) : cs_smem<float>(tile);
+}
+static int cs_threads(int tile) { return cs_is_bulk(tile) ? 32 + cs_tile_tx(tile) : cs_tile_tx(tile); }
+
+static cudaError_t cs_prepare(int precision, int tile) {
+    static bool done[2][CS_NTILES] = {};
+    const int p = precision == LBM_FP64 ? 0 : 1;
+    if (done[p][tile]) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (cs_bytes(precision, tile) > 0)
+        e = cudaFuncSetAttribute(cs_fn(precision, tile), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cs_bytes(precision, tile));
+    if (e == cudaSuccess) done[p][tile] = true;
+    return e;
+}
+
 cudaError_t launch_cs_step(int precision, int tile, int grid, const GroupDev& g, int j, cudaStream_t s) {
-    const void* fn = precision == LBM_FP64 ? cs_kernel_ptr<double>(tile) : cs_kernel_ptr<float>(tile);
-    if (!fn || grid <= 0) return cudaErrorInvalidValue;
+    if (tile < 0 || tile >= CS_NTILES || grid <= 0) return cudaErrorInvalidValue;
+    const void* fn = cs_fn(precision, tile);
+    cudaError_t e = cs_prepare(precision, tile);
+    if (e != cudaSuccess) return e;
     GroupDev gg = g;
     int jj = j;
     void* args[] = {&gg, &jj};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(cs_tile_tx(tile)), args, 0, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(cs_threads(tile)), args, cs_bytes(precision, tile), s);
 }
 
 int cs_blocks_per_sm(int precision, int tile) {
-    const void* fn = precision == LBM_FP64 ? cs_kernel_ptr<double>(tile) : cs_kernel_ptr<float>(tile);
+    if (tile < 0 || tile >= CS_NTILES || cs_prepare(precision, tile) != cudaSuccess) return 1;
     int n = 0;
-    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, cs_tile_tx(tile), 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cs_fn(precision, tile), cs_threads(tile),
+                                                      cs_bytes(precision, tile)) != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 

@@ -106,6 +106,9 @@ _SIGS = [
     ("lbm_batch_series", _i, [_P, _i, ctypes.POINTER(lbm_obs), _i64, ctypes.POINTER(_i64)]),
     ("lbm_batch_groups", _i, [_P, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _i]),
     ("lbm_batch_step_profiled", _i, [_P, _i64, _D, _i, _D]),
+    ("lbm_batch_config", _i, [_P, _i, _i, _i]),
+    ("lbm_config", _i, [_P, _i, _i]),
+    ("lbm_n_tiles", _i, [_i]),
     ("lbm_batch_kernel_launches", _i64, [_P]),
     ("lbm_kernel_launches", _i64, [_P]),
     ("lbm_batch_tune", _i, [_P, _i, ctypes.c_char_p, _sz]),
@@ -126,6 +129,10 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def lbm_n_tiles(model):
+    return lib().lbm_n_tiles(MODELS[model] if isinstance(model, str) else model)
 
 
 def exported_names():
@@ -321,6 +328,9 @@ class Lattice:
     def kernel_launches(self):
         return lib().lbm_kernel_launches(self._h)
 
+    def config(self, tile, grid=0):
+        check(lib().lbm_config(self._h, tile, grid), "lbm_config")
+
     def device_view(self):
         v = lbm_view()
         check(lib().lbm_device_view(self._h, ctypes.byref(v)), "lbm_device_view")
@@ -416,6 +426,9 @@ class Batch:
         m, q, p = (ctypes.c_int * G)(), (ctypes.c_int * G)(), (ctypes.c_int * G)()
         lib().lbm_batch_groups(self._h, m, q, p, G)
         return [dict(model=m[g], q=q[g], precision=p[g]) for g in range(G)]
+
+    def config(self, group, tile, grid=0):
+        check(lib().lbm_batch_config(self._h, group, tile, grid), "lbm_batch_config")
 
     def step_profiled(self, n):
         """Returns (per-group list of {kind: ms}, total ms)."""

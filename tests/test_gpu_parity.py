@@ -308,3 +308,50 @@ def test_fp32_fd_taylor_green_decay_rate():
     assert abs(g / g_ref - 1) < 1e-4, g / g_ref - 1
     _, u_ref, _ = oracle.macro(4, f)
     assert np.max(np.abs(u - u_ref)) / 0.01 < 5e-5
+
+
+# ---------------------------------------------------------------- every kernel variant
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx,ny", [(300, 70), (256, 64), (5, 3), (1, 1)])
+def test_cs_every_tile_variant(prec, nx, ny):
+    """Each CS kernel variant (plain and warp-specialised bulk-copy) gives
+    bit-identical states; FP64 ones also match the oracle."""
+    from paper_1904_02471_gb300 import lbm
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=nx + ny, amp_rho=0.1, amp_u=0.1)
+    f0 = oracle.equilibrium(3, rho, ux, uy)
+    tau = 0.47
+    res = []
+    for tile in range(lbm.lbm_n_tiles("cs")):
+        for grid in (0, 1, 7):
+            with pkg.Lattice("cs", 3, nx, ny, tau, precision=prec) as L:
+                L.config(tile, grid)
+                L.set_populations(f0)
+                L.step(37)
+                L.sync()
+                res.append(((tile, grid), L.populations()))
+    for cfg, f in res[1:]:
+        assert np.array_equal(f, res[0][1]), cfg
+    if prec == "fp64":
+        assert rel_err(res[0][1], oracle.cs_run(f0, tau, 37)) < TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("q,nx,ny", [(4, 70, 37), (5, 33, 20), (3, 8, 5)])
+def test_fd_every_tile_variant(prec, q, nx, ny):
+    from paper_1904_02471_gb300 import lbm
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=q + nx, amp_rho=0.1, amp_u=0.1)
+    f0 = oracle.equilibrium(q, rho, ux, uy)
+    dx = 1.0 / nx
+    dt, tau = 0.3 * dx / 3.0, 0.6 * dx / 3.0
+    res = []
+    for tile in range(lbm.lbm_n_tiles("fd")):
+        for grid in (0, 3):
+            with pkg.Lattice("fd", q, nx, ny, tau, dt=dt, precision=prec) as L:
+                L.config(tile, grid)
+                L.set_populations(f0)
+                L.step(12)
+                res.append(((tile, grid), L.populations()))
+    for cfg, f in res[1:]:
+        assert np.array_equal(f, res[0][1]), cfg
+    if prec == "fp64":
+        assert rel_err(res[0][1], oracle.fd_run(f0, dx, dt, tau, 12)) < TOL64
