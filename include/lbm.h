@@ -307,6 +307,40 @@ int64_t lbm_kernel_launches(const lbm_ctx* ctx);
  * report (may be NULL) of report_len bytes. */
 int lbm_batch_tune(lbm_batch* b, int trial_steps, char* report, size_t report_len);
 
+/* ---- observables without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code issued while a stream is being
+ * captured into a CUDA graph (cudaMalloc is not capturable), hosts that hand
+ * out a fixed memory arena and forbid further allocation, and
+ * latency-sensitive loops where cudaMalloc would synchronise the device.
+ *
+ * It computes what lbm_observables computes (float64 mass, momentum and
+ * probe amplitude) for a state in caller-owned device memory, and allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library call. Its scratch
+ * (block partial sums) is a file-scope device array of 1024 x 4 doubles
+ * (32 KiB) that every GPU loading the library holds until the process exits;
+ * larger lattices are covered by fewer, longer-striding blocks.
+ *
+ *  state: device pointer; element (k, y, x) at state + k*plane + y*pitch + x,
+ *      float64 full f (LBM_FP64) or float32 f - w_k rho0 (LBM_FP32_DEV). A CS
+ *      state is in the storage phase lbm_device_view reports
+ *      (f_k(x) = stored_k(x - c_k)); FD states are f itself.
+ *  comp: -1 for no probe, else 0 (u_x) / 1 (u_y) with device tables px[nx],
+ *      py[ny] and norm as in lbm_set_probe.
+ *  step, dt: copied into the record (time = step * dt).
+ *  out: device pointer to one lbm_obs, written asynchronously on cuda_stream
+ *      (NULL = legacy default stream); the call returns after enqueueing.
+ * Limits: nx*ny < 2^31, pitch >= nx, plane >= pitch*ny; LBM_EINVAL otherwise.
+ * The first call on a device looks up the array's device address with that
+ * device current (once per device); make that first call before any stream
+ * capture. Every call shares the one array and overwrites all of it that it
+ * reads, so calls do not depend on each other's leftovers, but calls that
+ * overlap on the GPU (different streams, no ordering) race on the array. */
+int lbm_observables_noalloc(int model, int q_per_axis, int precision, int nx, int ny, const void* state,
+                            int64_t plane, int32_t pitch, double rho0, int comp, const double* px,
+                            const double* py, double norm, int64_t step, double dt, lbm_obs* out,
+                            void* cuda_stream);
+
 /* ---- errors ---------------------------------------------------------------- */
 const char* lbm_strerror(int code);
 const char* lbm_last_error(void);

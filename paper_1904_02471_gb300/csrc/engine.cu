@@ -18,10 +18,14 @@
 
 namespace lbm {
 
-static thread_local std::string g_last_error;
+static thread_local char g_last_error[512];
 
-void set_error(const std::string& msg) { g_last_error = msg; }
-const char* last_error_cstr() { return g_last_error.c_str(); }
+void set_error(const char* msg) {
+    size_t i = 0;
+    for (; msg && msg[i] && i + 1 < sizeof g_last_error; ++i) g_last_error[i] = msg[i];
+    g_last_error[i] = 0;
+}
+const char* last_error_cstr() { return g_last_error; }
 
 int cuda_fail(cudaError_t e, const char* what) {
     char buf[256];

@@ -15,8 +15,10 @@ namespace lbm {
 
 constexpr long long UNLIMITED = (1LL << 62);
 
-// Thread-local detail of the last error, returned by lbm_last_error().
-void set_error(const std::string& msg);
+// Thread-local detail of the last error, returned by lbm_last_error(); kept
+// in a fixed buffer, so recording an error never allocates.
+void set_error(const char* msg);
+inline void set_error(const std::string& msg) { set_error(msg.c_str()); }
 int cuda_fail(cudaError_t e, const char* what);
 
 struct Lattice {

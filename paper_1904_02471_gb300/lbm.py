@@ -112,6 +112,8 @@ _SIGS = [
     ("lbm_batch_kernel_launches", _i64, [_P]),
     ("lbm_kernel_launches", _i64, [_P]),
     ("lbm_batch_tune", _i, [_P, _i, ctypes.c_char_p, _sz]),
+    ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, _d, _i, _P, _P, _d, _i64, _d,
+                                     _P, _P]),
 ]
 
 
