@@ -42,6 +42,7 @@ FD_DT = 1e-5
 FD_TAU = 5e-4
 CS_TAU = 0.8 / math.sqrt(3.0)
 U0 = 0.01
+FD_CFL = 0.4
 METRIC = "MLUPS & % HBM roofline, CS and FD; batched FP32 vs plain FP64; p50/p99"
 WORKLOAD = "roofline lattices: CS D2Q9 8192^2 + FD 16-velocity 4096^2, FP32 deviation storage, Taylor-Green"
 # algorithmic bytes per lattice update (FP32): CS reads and writes 9 values;
@@ -203,11 +204,8 @@ def run_gpu(args, rank, world):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_max = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    from paper_1904_02471_gb300 import replicas
+    t_max = replicas.job_time(dist, total_ms, device="cuda")
 
     # check the run stayed finite and conserved mass (float64 sums)
     ser = [B.series(i) for i in range(2)]
@@ -234,7 +232,7 @@ def run_gpu(args, rank, world):
     fd_stage_ms = [ms[gfd][s] / K for s in range(3)]
     fin_ms = (ms[gcs][3] + ms[gfd][3]) / K
     cells = CS_N * CS_N + FD_N * FD_N
-    value = world * cells * K / (t_max / 1e3) / 1e6
+    value = replicas.whole_job_rate(cells * K, world, t_max / 1e3) / 1e6
     cs_gbs = CS_N * CS_N * CS_BYTES_LU / (cs_ms / 1e3) / 1e9
     fd_stage_avg = sum(fd_stage_ms) / 3
     fd_gbs = FD_N * FD_N * FD_BYTES_LU / 3 / (fd_stage_avg / 1e3) / 1e9
@@ -282,6 +280,9 @@ def run_gpu(args, rank, world):
         "checks": {"finite": finite, "rel_mass_drift": [float(f"{d:.3e}") for d in drift],
                    "host_wall_s": round(wall, 4)},
     }
+    if not args.no_extras:
+        rec["batched"] = run_batched(torch)
+        rec["served"] = run_served(torch)
     if rates is not None:
         rec["cpu_baseline"] = {"value": round(cpu_value(rates), 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                                "sample": f"{rates['cs_sample']}; {rates['fd_sample']}; FP64 C oracle, one thread, "
@@ -290,6 +291,138 @@ def run_gpu(args, rank, world):
     if dist:
         dist.destroy_process_group()
     return rec
+
+
+# ---------------------------------------------------------------- batched + served
+def _instance_spec(pkg, d, prec):
+    """Spec of one batched/served instance: CS D2Q9 with tau_LU = tau*/sqrt 3,
+    or FD 16-velocity with tau_FD from Eq. (nu-transfer) and the largest
+    stable time step (CFL and dt <= tau)."""
+    n = d["n"]
+    tau_lu = d["tau_star"] / math.sqrt(3.0)
+    if d["model"] == "cs":
+        return pkg.make_spec("cs", 3, n, n, tau_lu, 0.0, 0.0, prec)
+    tau_fd = pkg.lbm_tau_fd_from_lu(n, tau_lu)
+    return pkg.make_spec("fd", 4, n, n, tau_fd, fd_dt(pkg, 4, n, tau_fd), 0.0, prec)
+
+
+def fd_dt(pkg, q, n, tau_fd, cfl=FD_CFL):
+    """FD time step of the synthetic workloads: dt <= tau (Sec. 4.1) and a
+    Courant number max|v| dt/dx of FD_CFL. CFL = 1, the bound Sec. 4.1 states
+    for its quasi-1D runs, is not stable for WENO-5 + RK3 advection along
+    both axes at once."""
+    return min(tau_fd, cfl * pkg.lbm_fd_max_dt(q, 1.0 / n, 1e300))
+
+
+def _fields(d):
+    n = d["n"]
+    U = U0 * (math.sqrt(3.0) if d["model"] == "cs" else 1.0)
+    return wl.shear_wave(n, n, U) if d.get("init") == "shear" else wl.taylor_green(n, n, U)
+
+
+def run_batched(torch, steps=192, plain_steps=2):
+    """256 independent lattices (sides from {32..512}, tau* in [0.51, 2], half
+    CS, half FD 16-velocity): all advanced together in FP32 (one persistent
+    launch per group and step, graph replays) against the plain form, each
+    lattice alone in FP64, one at a time."""
+    import paper_1904_02471_gb300 as pkg
+    inst = wl.batched_instances(256, seed=0)
+    cells = sum(d["n"] ** 2 for d in inst)
+    B = pkg.Batch([_instance_spec(pkg, d, "fp32") for d in inst])
+    for i, d in enumerate(inst):
+        B.init(i, *_fields(d))
+    tune = B.tune(2)
+    B.step(32)
+    B.sync()
+    t0 = time.perf_counter()
+    B.step(steps)
+    B.sync()
+    t_b = time.perf_counter() - t0
+    mlups_b = cells * steps / t_b / 1e6
+    # accuracy of the FP32 batch against FP64 runs of the same lattices
+    probe = [i for i, d in enumerate(inst) if d["n"] <= 64][:4]
+    got = {i: B.moments(i) for i in probe}
+    done = B.steps_done(probe[0]) if probe else 0
+    B.close()
+    err = 0.0
+    for i in probe:
+        d = inst[i]
+        with pkg.Lattice(**_lat_kwargs(pkg, d, "fp64")) as L:
+            L.init(*_fields(d))
+            L.step(done)
+            _, u, v = L.moments()
+        U = U0 * (math.sqrt(3.0) if d["model"] == "cs" else 1.0)
+        err = max(err, float(np.max(np.abs(got[i][1] - u))) / U, float(np.max(np.abs(got[i][2] - v))) / U)
+    # plain: FP64, one lattice at a time
+    t_plain, work = 0.0, 0
+    per_model = {"cs": [0, 0.0], "fd": [0, 0.0]}
+    for d in inst:
+        with pkg.Lattice(**_lat_kwargs(pkg, d, "fp64")) as L:
+            L.init(*_fields(d))
+            L.step(1)
+            L.sync()
+            t0 = time.perf_counter()
+            L.step(plain_steps)
+            L.sync()
+            dt = time.perf_counter() - t0
+        t_plain += dt
+        work += d["n"] ** 2 * plain_steps
+        per_model[d["model"]][0] += d["n"] ** 2 * plain_steps
+        per_model[d["model"]][1] += dt
+    mlups_p = work / t_plain / 1e6
+    return {
+        "workload": "256 lattices, sides uniform in {32,64,128,256,512}, tau* U[0.51,2], half CS D2Q9 / half FD "
+                    "16-velocity, shear-wave and Taylor-Green initial states (seed 0)",
+        "cells": cells,
+        "fp32_batched": {"mlups": round(mlups_b, 1), "steps": steps, "s": round(t_b, 4), "tuning": tune.strip()},
+        "fp64_plain_one_at_a_time": {
+            "mlups": round(mlups_p, 2), "steps_each": plain_steps,
+            "cs_mlups": round(per_model["cs"][0] / max(per_model["cs"][1], 1e-12) / 1e6, 2),
+            "fd_mlups": round(per_model["fd"][0] / max(per_model["fd"][1], 1e-12) / 1e6, 2)},
+        "speedup": round(mlups_b / mlups_p, 1),
+        "fp32_vs_fp64_max_rel_velocity_error": float(f"{err:.3e}"),
+        "accuracy_sample": f"{len(probe)} lattices (side <= 64) after {done} steps",
+    }
+
+
+def _lat_kwargs(pkg, d, prec):
+    s = _instance_spec(pkg, d, prec)
+    return dict(model="cs" if s.model == 0 else "fd", q=s.q_per_axis, nx=s.nx, ny=s.ny, tau=s.tau, dt=s.dt,
+                precision=prec)
+
+
+def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=(1000, 5000), duration_s=30.0):
+    """Served stream: Poisson arrivals of CS / FD Taylor-Green runs (FP32)
+    into the continuous-batching server; latency = completion - arrival."""
+    import paper_1904_02471_gb300 as pkg
+    from paper_1904_02471_gb300 import lbm
+    reqs = wl.served_stream(n_req, seed, rate_per_s=n_req / duration_s, sides=sides, steps=steps)
+    work = sum(r["n"] ** 2 * r["steps"] for r in reqs)
+    S = lbm.Server(64 << 30, 256, 128)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        delay = r["arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        spec = _instance_spec(pkg, {"model": r["model"], "n": r["n"], "tau_star": r["tau_star"]}, "fp32")
+        U = U0 * (math.sqrt(3.0) if r["model"] == "cs" else 1.0)
+        tickets.append(S.submit(lbm.make_request(spec, r["steps"], "tg", U, obs_every=0)))
+    S.drain(1800)
+    res = [S.poll(t) for t in tickets]
+    S.close()
+    lat = sorted(x["t_done"] - x["t_submit"] for x in res)
+    makespan = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+    ok = sum(1 for x in res if x["status"] == 0)
+    return {
+        "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{duration_s:.0f} s, CS or FD 16-velocity "
+                    f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2), steps U[{steps[0]},{steps[1]}], FP32",
+        "requests": n_req, "completed_ok": ok,
+        "aggregate_mlups": round(work / makespan / 1e6, 1),
+        "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4), "p99": round(float(np.percentile(lat, 99)), 4),
+                      "max": round(lat[-1], 4)},
+        "makespan_s": round(makespan, 3),
+    }
 
 
 def committed_traffic():
@@ -345,6 +478,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

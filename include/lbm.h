@@ -307,6 +307,72 @@ int64_t lbm_kernel_launches(const lbm_ctx* ctx);
  * report (may be NULL) of report_len bytes. */
 int lbm_batch_tune(lbm_batch* b, int trial_steps, char* report, size_t report_len);
 
+/* ---- continuous-batching run server -------------------------------------- */
+
+/* A request: one complete run of `steps` steps from an initial state:
+ * init 0: Taylor-Green vortex, Sec. 4.3 Eq. (tg), density from the steady
+ *         pressure balance; 1: shear wave, Sec. 4.2; 2: shock tube, Sec. 4.1,
+ *         rho_l for x <= nx/2 else rho_r, fluid at rest.
+ * U is the velocity amplitude in the model's units. obs_every > 0 records the
+ * observables every obs_every steps (fused into the step kernels) and fits
+ * the apparent viscosity of the decay (init 0 and 1); 0 records only the
+ * first and last state. user_tag is returned unchanged. */
+typedef struct {
+    lbm_spec spec;
+    int64_t steps;
+    int init;
+    int obs_every;
+    double U;
+    double rho_l, rho_r;
+    uint64_t user_tag;
+} lbm_request;
+
+/* Result of a finished request. status: LBM_OK, LBM_ENONFINITE, LBM_ECANCELLED,
+ * LBM_ENOMEM (admission failed), LBM_ECUDA. Times are seconds on the server's
+ * clock (since creation): latency = t_done - t_submit. nu_fit: apparent
+ * viscosity gamma/(m k^2) from a log-linear fit of the recorded amplitude
+ * (m = 1 shear, 2 Taylor-Green; Sec. 4.2-4.3), in the model's units; 0 when
+ * not available. */
+typedef struct {
+    int status;
+    int reserved;
+    uint64_t user_tag;
+    int64_t steps;
+    lbm_obs first, last;
+    double nu_fit;
+    double t_submit, t_admit, t_done;
+    int64_t n_series;
+} lbm_result;
+
+typedef struct lbm_server lbm_server;
+
+/* Start a server with a worker thread. hbm_budget_bytes bounds the summed
+ * device footprint of resident runs (admission control); max_slots bounds
+ * their number; chunk_steps is the number of steps per scheduling round.
+ * cuda_stream as in lbm_create. A server is thread-safe. */
+int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, int chunk_steps,
+                      void* cuda_stream);
+/* Queue a request and return at once with its ticket. LBM_EINVAL / LBM_ECFL /
+ * LBM_ESTIFF for a bad spec (as lbm_create), LBM_ENOMEM if its footprint
+ * exceeds the whole budget. */
+int lbm_submit(lbm_server* s, const lbm_request* req, uint64_t* ticket);
+/* LBM_ENOTREADY until the run finished, then LBM_OK and *out filled;
+ * LBM_ENOTFOUND for an unknown ticket. */
+int lbm_poll(lbm_server* s, uint64_t ticket, lbm_result* out);
+/* Copy up to cap recorded observables of a finished run; *count receives how
+ * many there are. */
+int lbm_result_series(lbm_server* s, uint64_t ticket, lbm_obs* out, int64_t cap, int64_t* count);
+/* Cancel a queued or running request (a running one stops at the end of the
+ * current round with status LBM_ECANCELLED). */
+int lbm_cancel(lbm_server* s, uint64_t ticket);
+/* Wait until every submitted request finished, or timeout_s (LBM_ETIMEOUT). */
+int lbm_server_drain(lbm_server* s, double timeout_s);
+/* Queued, running and finished counts and resident device bytes. */
+int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* finished,
+                     size_t* resident_bytes);
+/* Cancel what is left, stop the worker and free everything. */
+void lbm_server_destroy(lbm_server* s);
+
 /* ---- observables without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory: code issued while a stream is being

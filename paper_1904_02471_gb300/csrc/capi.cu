@@ -310,7 +310,7 @@ void lbm_batch_destroy(lbm_batch* b) {
 int lbm_batch_size(const lbm_batch* b) { return b ? const_cast<lbm_batch*>(b)->e.n_lattices() : 0; }
 
 #define BATCH_IDX_CHECK(b, i) \
-    if (!(b) || (i) < 0 || (i) >= (b)->e.n_lattices()) return LBM_EINVAL
+    if (!(b) || !(b)->e.valid(i)) return LBM_EINVAL
 
 int lbm_batch_init(lbm_batch* b, int i, const double* rho, const double* ux, const double* uy) {
     GUARD_BEGIN

@@ -99,17 +99,7 @@ int Engine::validate(const lbm_spec* in, lbm_spec* out) {
 Engine::~Engine() {
     if (stream_) cudaStreamSynchronize(stream_);
     invalidate_graph();
-    for (auto& L : lat) {
-        cudaFree(L.mem);
-        cudaFree(L.d_px);
-        cudaFree(L.d_py);
-        cudaFree(L.d_pxf);
-        cudaFree(L.d_pyf);
-        cudaFree(L.d_series);
-        cudaFree(L.d_io);
-        cudaFree(L.d_part);
-        cudaFree(L.d_snap);
-    }
+    for (auto& L : lat) free_lattice(L);
     for (auto& g : groups) {
         cudaFree(g.d_desc);
         cudaFree(g.d_item_begin);
@@ -129,8 +119,115 @@ void Engine::invalidate_graph() {
 int Engine::default_grid(const Group& g, int tile) const {
     int bps = g.model == LBM_CS ? cs_blocks_per_sm(g.precision, tile) : fd_blocks_per_sm(g.precision, g.q1, tile);
     long long grid = (long long)sm_count_ * bps;
-    if (g.total_items > 0 && grid > g.total_items) grid = g.total_items;
+    if (!dynamic_ && g.total_items > 0 && grid > g.total_items) grid = g.total_items;
     return (int)std::max<long long>(1, grid);
+}
+
+int Engine::open(void* stream) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev));
+    if (stream) {
+        stream_ = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+        own_stream_ = true;
+    }
+    return LBM_OK;
+}
+
+void Engine::free_lattice(Lattice& L) {
+    cudaFree(L.mem);
+    cudaFree(L.d_px);
+    cudaFree(L.d_py);
+    cudaFree(L.d_pxf);
+    cudaFree(L.d_pyf);
+    cudaFree(L.d_series);
+    cudaFree(L.d_io);
+    cudaFree(L.d_part);
+    cudaFree(L.d_snap);
+    L.mem = L.d_io = nullptr;
+    L.d_px = L.d_py = L.d_part = L.d_snap = nullptr;
+    L.d_pxf = L.d_pyf = nullptr;
+    L.d_series = nullptr;
+    for (auto& b : L.buf) b = nullptr;
+    L.io_bytes = 0;
+}
+
+size_t Engine::footprint(const lbm_spec& s) {
+    const int K = s.q_per_axis * s.q_per_axis;
+    const long long pitch = (s.nx + 8 + 31) / 32 * 32;
+    const long long plane = pitch * s.ny;
+    const int nbuf = s.model == LBM_CS ? 2 : 3;
+    const int elem = s.precision == LBM_FP64 ? 8 : 4;
+    return (size_t)nbuf * (K * plane + Lattice::TAIL) * elem + sizeof(double) * NOBS * 1024;
+}
+
+int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
+    Lattice L;
+    const int rc = validate(spec, &L.spec);
+    if (rc != LBM_OK) return rc;
+    const lbm_spec& s = L.spec;
+    L.K = s.q_per_axis * s.q_per_axis;
+    L.elem = s.precision == LBM_FP64 ? 8 : 4;
+    L.pitch = (s.nx + 8 + 31) / 32 * 32;
+    L.plane = (long long)L.pitch * s.ny;
+    L.nbuf = s.model == LBM_CS ? 2 : 3;
+    L.rho0s = s.precision == LBM_FP64 ? 0.0 : s.rho0;
+    if (s.model == LBM_CS) {
+        L.omega = s.dt / s.tau;
+    } else {
+        L.cdx = s.dt / s.dx;
+        L.dt_tau = s.dt / s.tau;
+    }
+    const size_t bytes = L.state_bytes();
+    cudaError_t e = cudaMalloc(&L.mem, bytes);
+    if (e != cudaSuccess) {
+        L.mem = nullptr;
+        return cuda_fail(e, "cudaMalloc(state)");
+    }
+    e = cudaMemsetAsync(L.mem, 0, bytes, stream_);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_part, sizeof(double) * NOBS * 1024);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_snap, sizeof(double) * NOBS);
+    if (e != cudaSuccess) {
+        free_lattice(L);
+        return cuda_fail(e, "lattice allocation");
+    }
+    L.part_blocks = 1024;
+    for (int b = 0; b < L.nbuf; ++b)
+        L.buf[b] = static_cast<char*>(L.mem) + (b * L.buf_stride() + Lattice::HEAD) * L.elem;
+    // group membership: one group per (model, velocity set, storage)
+    int gi = -1;
+    for (size_t g = 0; g < groups.size(); ++g)
+        if (groups[g].model == s.model && groups[g].q1 == s.q_per_axis && groups[g].precision == s.precision) gi = (int)g;
+    if (gi < 0) {
+        Group g;
+        g.model = s.model;
+        g.q1 = s.q_per_axis;
+        g.precision = s.precision;
+        g.tile = s.model == LBM_CS ? (int)CS_B256x32 : (int)FD_T32x8;
+        groups.push_back(g);
+        gi = (int)groups.size() - 1;
+        invalidate_graph();
+    }
+    L.group = gi;
+    const int idx = (int)lat.size();
+    lat.push_back(L);
+    groups[gi].members.push_back(idx);
+    if (index) *index = idx;
+    return upload ? upload_group(gi) : LBM_OK;
+}
+
+int Engine::remove_lattice(int i) {
+    if (!valid(i) || !lat[i].alive) { set_error("no such lattice"); return LBM_EINVAL; }
+    CK(cudaStreamSynchronize(stream_));
+    Lattice& L = lat[i];
+    Group& g = groups[L.group];
+    g.members.erase(std::remove(g.members.begin(), g.members.end(), i), g.members.end());
+    free_lattice(L);
+    L.alive = false;
+    L.active = false;
+    return upload_group(L.group);
 }
 
 int Engine::create(const lbm_spec* specs, int n, void* stream) {
@@ -145,57 +242,12 @@ int Engine::create(const lbm_spec* specs, int n, void* stream) {
             return rc;
         }
     }
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev));
-    if (stream) {
-        stream_ = static_cast<cudaStream_t>(stream);
-    } else {
-        CK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
-        own_stream_ = true;
-    }
-    lat.resize(n);
+    int rc = open(stream);
+    if (rc) return rc;
+    lat.reserve(n);
     for (int i = 0; i < n; ++i) {
-        Lattice& L = lat[i];
-        validate(&specs[i], &L.spec);
-        const lbm_spec& s = L.spec;
-        L.K = s.q_per_axis * s.q_per_axis;
-        L.elem = s.precision == LBM_FP64 ? 8 : 4;
-        L.pitch = (s.nx + 8 + 31) / 32 * 32;
-        L.plane = (long long)L.pitch * s.ny;
-        L.nbuf = s.model == LBM_CS ? 2 : 3;
-        L.rho0s = s.precision == LBM_FP64 ? 0.0 : s.rho0;
-        if (s.model == LBM_CS) {
-            L.omega = s.dt / s.tau;
-        } else {
-            L.cdx = s.dt / s.dx;
-            L.dt_tau = s.dt / s.tau;
-        }
-        const size_t bytes = L.state_bytes();
-        cudaError_t e = cudaMalloc(&L.mem, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
-        CK(cudaMemsetAsync(L.mem, 0, bytes, stream_));
-        for (int b = 0; b < L.nbuf; ++b)
-            L.buf[b] = static_cast<char*>(L.mem) + (b * L.buf_stride() + Lattice::HEAD) * L.elem;
-        L.part_blocks = 1024;
-        CK(cudaMalloc(&L.d_part, sizeof(double) * NOBS * L.part_blocks));
-        CK(cudaMalloc(&L.d_snap, sizeof(double) * NOBS));
-        // group membership
-        int gi = -1;
-        for (size_t g = 0; g < groups.size(); ++g)
-            if (groups[g].model == s.model && groups[g].q1 == s.q_per_axis && groups[g].precision == s.precision) gi = (int)g;
-        if (gi < 0) {
-            Group g;
-            g.model = s.model;
-            g.q1 = s.q_per_axis;
-            g.precision = s.precision;
-            g.tile = s.model == LBM_CS ? (int)CS_T128x2 : (int)FD_T32x8;
-            groups.push_back(g);
-            gi = (int)groups.size() - 1;
-        }
-        L.group = gi;
-        L.slot = (int)groups[gi].members.size();
-        groups[gi].members.push_back(i);
+        rc = add_lattice(&specs[i], nullptr, false);
+        if (rc) return rc;
     }
     return upload_all();
 }
@@ -244,6 +296,7 @@ int Engine::upload_group(int gi) {
     const int ty = g.model == LBM_CS ? cs_tile_ty(g.tile) : fd_tile_ty(g.tile);
     std::vector<int> begins;
     long long items = 0;
+    const bool had_obs = g.any_obs;
     g.any_obs = false;
     for (int li : g.members) {
         const Lattice& L = lat[li];
@@ -252,6 +305,7 @@ int Engine::upload_group(int gi) {
         if (L.obs_every > 0) g.any_obs = true;
     }
     if (items >= (1LL << 31)) { set_error("too many work items"); return LBM_EINVAL; }
+    if (g.any_obs != had_obs) invalidate_graph();
     const int nm = (int)g.members.size();
     if (nm > g.cap_lat) {
         cudaFree(g.d_desc);
@@ -260,7 +314,7 @@ int Engine::upload_group(int gi) {
         g.d_desc = nullptr;
         g.d_item_begin = nullptr;
         g.d_hdr = nullptr;
-        const int cap = std::max(nm, 1);
+        const int cap = std::max(std::max(nm, 1), dynamic_ ? 2 * g.cap_lat : 0);  // grow geometrically
         CK(cudaMalloc(&g.d_desc, sizeof(LatDesc) * cap));
         CK(cudaMalloc(&g.d_item_begin, sizeof(int) * cap));
         CK(cudaMalloc(&g.d_hdr, sizeof(int) * 4));
@@ -270,8 +324,9 @@ int Engine::upload_group(int gi) {
     if (items > g.cap_items) {
         cudaFree(g.d_partials);
         g.d_partials = nullptr;
-        CK(cudaMalloc(&g.d_partials, sizeof(double) * NOBS * std::max<long long>(items, 1)));
-        g.cap_items = std::max<long long>(items, 1);
+        const long long cap = std::max(std::max<long long>(items, 1), dynamic_ ? 2 * g.cap_items : 0);
+        CK(cudaMalloc(&g.d_partials, sizeof(double) * NOBS * cap));
+        g.cap_items = cap;
         invalidate_graph();
     }
     g.total_items = (int)items;
@@ -280,7 +335,9 @@ int Engine::upload_group(int gi) {
         const Lattice& L = lat[li];
         max_items = std::max<long long>(max_items, (long long)((L.spec.nx + tx - 1) / tx) * ((L.spec.ny + ty - 1) / ty));
     }
-    const int nch = (int)std::min<long long>(128, std::max<long long>(1, (max_items + 2047) / 2048));
+    // chunks of the observables reduction; fixed for dynamic engines so that
+    // membership changes do not change the captured launches
+    const int nch = dynamic_ ? 128 : (int)std::min<long long>(128, std::max<long long>(1, (max_items + 2047) / 2048));
     if (nch != g.nchunks || (long long)g.cap_lat * nch > g.chunk_cap || !g.d_chunks) {
         cudaFree(g.d_chunks);
         g.d_chunks = nullptr;
@@ -290,8 +347,10 @@ int Engine::upload_group(int gi) {
         invalidate_graph();
     }
     std::vector<LatDesc> descs;
-    for (int m = 0; m < nm; ++m)
+    for (int m = 0; m < nm; ++m) {
+        lat[g.members[m]].slot = m;
         descs.push_back(make_desc(lat[g.members[m]], g, begins[m], g.d_partials + (long long)begins[m] * NOBS));
+    }
     const int hdr[4] = {nm, (int)items, 0, 0};
     if (nm) {
         CK(cudaMemcpyAsync(g.d_desc, descs.data(), sizeof(LatDesc) * nm, cudaMemcpyHostToDevice, stream_));
@@ -333,7 +392,7 @@ int Engine::enqueue_chunk(int c) {
     long long n = 0;
     for (int j = 0; j < c; ++j) {
         for (auto& g : groups) {
-            if (g.members.empty()) continue;
+            if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
             const GroupDev gd = g.dev();
             cudaError_t e;
             if (g.model == LBM_CS) {
@@ -341,7 +400,7 @@ int Engine::enqueue_chunk(int c) {
                 if (e != cudaSuccess) return cuda_fail(e, "launch_cs_step");
                 ++n;
                 if (g.any_obs) {
-                    if ((e = launch_obs_finalize(gd, (int)g.members.size(), g.nchunks, g.d_chunks, j, stream_)) != cudaSuccess)
+                    if ((e = launch_obs_finalize(gd, g.cap_lat, g.nchunks, g.d_chunks, j, stream_)) != cudaSuccess)
                         return cuda_fail(e, "launch_obs_finalize");
                     n += 2;
                 }
@@ -351,7 +410,7 @@ int Engine::enqueue_chunk(int c) {
                     if (e != cudaSuccess) return cuda_fail(e, "launch_fd_stage");
                     ++n;
                     if (st == 1 && g.any_obs) {
-                        if ((e = launch_obs_finalize(gd, (int)g.members.size(), g.nchunks, g.d_chunks, j, stream_)) != cudaSuccess)
+                        if ((e = launch_obs_finalize(gd, g.cap_lat, g.nchunks, g.d_chunks, j, stream_)) != cudaSuccess)
                             return cuda_fail(e, "launch_obs_finalize");
                         n += 2;
                     }
@@ -360,8 +419,8 @@ int Engine::enqueue_chunk(int c) {
         }
     }
     for (auto& g : groups) {
-        if (g.members.empty()) continue;
-        cudaError_t e = launch_advance(g.dev(), (int)g.members.size(), c, g.model == LBM_CS ? 1 : 0, stream_);
+        if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
+        cudaError_t e = launch_advance(g.dev(), g.cap_lat, c, g.model == LBM_CS ? 1 : 0, stream_);
         if (e != cudaSuccess) return cuda_fail(e, "launch_advance");
         ++n;
     }
@@ -371,7 +430,7 @@ int Engine::enqueue_chunk(int c) {
 
 void Engine::mirror_advance(int c) {
     for (auto& L : lat) {
-        if (!L.active) continue;
+        if (!L.alive || !L.active) continue;
         const long long adv = std::min<long long>(L.remaining, c);
         L.step0 += adv;
         L.remaining -= adv;
@@ -440,7 +499,7 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
     for (long long s = 0; s < n; ++s) {
         for (int gi = 0; gi < G; ++gi) {
             Group& g = groups[gi];
-            if (g.members.empty()) continue;
+            if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
             const GroupDev gd = g.dev();
             const int nk = g.model == LBM_CS ? 1 : 3;
             for (int st = 1; st <= nk; ++st) {
@@ -457,7 +516,7 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
                     cudaEvent_t c = ev(), d = ev();
                     if (!c || !d) { cleanup(); return cuda_fail(cudaGetLastError(), "cudaEventCreate"); }
                     cudaEventRecord(c, stream_);
-                    e = launch_obs_finalize(gd, (int)g.members.size(), g.nchunks, g.d_chunks, 0, stream_);
+                    e = launch_obs_finalize(gd, g.cap_lat, g.nchunks, g.d_chunks, 0, stream_);
                     cudaEventRecord(d, stream_);
                     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "profiled finalize"); }
                     launches_ += 2;
@@ -466,8 +525,8 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
             }
         }
         for (auto& g : groups) {
-            if (g.members.empty()) continue;
-            cudaError_t e = launch_advance(g.dev(), (int)g.members.size(), 1, g.model == LBM_CS ? 1 : 0, stream_);
+            if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
+            cudaError_t e = launch_advance(g.dev(), g.cap_lat, 1, g.model == LBM_CS ? 1 : 0, stream_);
             if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "launch_advance"); }
             ++launches_;
         }
@@ -534,7 +593,7 @@ static bool all_finite(const double* a, size_t n) {
 }
 
 int Engine::init(int i, const double* rho, const double* ux, const double* uy) {
-    if (i < 0 || i >= (int)lat.size() || !rho || !ux || !uy) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !rho || !ux || !uy) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     const size_t n = (size_t)L.spec.nx * L.spec.ny;
     for (size_t c = 0; c < n; ++c)
@@ -559,7 +618,7 @@ int Engine::init(int i, const double* rho, const double* ux, const double* uy) {
 }
 
 int Engine::set_populations(int i, const double* f) {
-    if (i < 0 || i >= (int)lat.size() || !f) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !f) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     const size_t n = (size_t)L.spec.nx * L.spec.ny * L.K;
     if (!all_finite(f, n)) { set_error("populations must be finite"); return LBM_EINVAL; }
@@ -601,17 +660,17 @@ int Engine::readout(int i, double* f, double* rho, double* ux, double* uy, bool 
 }
 
 int Engine::moments(int i, double* rho, double* ux, double* uy) {
-    if (i < 0 || i >= (int)lat.size() || !rho || !ux || !uy) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !rho || !ux || !uy) { set_error("bad arguments"); return LBM_EINVAL; }
     return readout(i, nullptr, rho, ux, uy, false);
 }
 
 int Engine::populations(int i, double* f) {
-    if (i < 0 || i >= (int)lat.size() || !f) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !f) { set_error("bad arguments"); return LBM_EINVAL; }
     return readout(i, f, nullptr, nullptr, nullptr, false);
 }
 
 int Engine::populations_region(int i, int x0, int y0, int wx, int wy, double* f) {
-    if (i < 0 || i >= (int)lat.size() || !f) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !f) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     if (x0 < 0 || y0 < 0 || x0 >= L.spec.nx || y0 >= L.spec.ny || wx < 1 || wy < 1 || wx > L.spec.nx ||
         wy > L.spec.ny) {
@@ -630,7 +689,7 @@ int Engine::populations_region(int i, int x0, int y0, int wx, int wy, double* f)
 }
 
 int Engine::observables(int i, lbm_obs* out) {
-    if (i < 0 || i >= (int)lat.size() || !out) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || !out) { set_error("bad arguments"); return LBM_EINVAL; }
     int rc = readout(i, nullptr, nullptr, nullptr, nullptr, true);
     if (rc) return rc;
     Lattice& L = lat[i];
@@ -650,7 +709,7 @@ int Engine::observables(int i, lbm_obs* out) {
 }
 
 int Engine::set_probe(int i, int comp, const double* px, const double* py, double norm) {
-    if (i < 0 || i >= (int)lat.size() || (comp != 0 && comp != 1) || !px || !py || !std::isfinite(norm)) {
+    if (!valid(i) || (comp != 0 && comp != 1) || !px || !py || !std::isfinite(norm)) {
         set_error("bad probe arguments");
         return LBM_EINVAL;
     }
@@ -675,7 +734,7 @@ int Engine::set_probe(int i, int comp, const double* px, const double* py, doubl
 }
 
 int Engine::record(int i, long long every, long long cap) {
-    if (i < 0 || i >= (int)lat.size() || every < 0 || (every > 0 && cap < 1) || cap > (1LL << 30)) {
+    if (!valid(i) || every < 0 || (every > 0 && cap < 1) || cap > (1LL << 30)) {
         set_error("bad record arguments");
         return LBM_EINVAL;
     }
@@ -697,7 +756,7 @@ int Engine::record(int i, long long every, long long cap) {
 }
 
 int Engine::series(int i, lbm_obs* out, long long cap, long long* count) {
-    if (i < 0 || i >= (int)lat.size() || cap < 0 || (cap > 0 && !out)) { set_error("bad arguments"); return LBM_EINVAL; }
+    if (!valid(i) || cap < 0 || (cap > 0 && !out)) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     CK(cudaStreamSynchronize(stream_));
     long long n = 0;
@@ -710,10 +769,19 @@ int Engine::series(int i, lbm_obs* out, long long cap, long long* count) {
 }
 
 int Engine::set_budget(int i, long long steps) {
-    if (i < 0 || i >= (int)lat.size() || steps < 0) { set_error("bad budget"); return LBM_EINVAL; }
+    if (!valid(i) || steps < 0) { set_error("bad budget"); return LBM_EINVAL; }
     CK(cudaStreamSynchronize(stream_));
     lat[i].remaining = steps;
     return upload_group(lat[i].group);
+}
+
+int Engine::release_io(int i) {
+    if (!valid(i)) { set_error("bad arguments"); return LBM_EINVAL; }
+    CK(cudaStreamSynchronize(stream_));
+    cudaFree(lat[i].d_io);
+    lat[i].d_io = nullptr;
+    lat[i].io_bytes = 0;
+    return LBM_OK;
 }
 
 int Engine::set_eps(int i, double eps) {
@@ -741,7 +809,7 @@ size_t Engine::checkpoint_size(int i) const {
 }
 
 int Engine::save(int i, void* buf, size_t size) {
-    if (i < 0 || i >= (int)lat.size() || !buf || size < checkpoint_size(i)) { set_error("checkpoint buffer too small"); return LBM_EINVAL; }
+    if (!valid(i) || !buf || size < checkpoint_size(i)) { set_error("checkpoint buffer too small"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     CkptHeader h;
     memset(&h, 0, sizeof h);
@@ -758,7 +826,7 @@ int Engine::save(int i, void* buf, size_t size) {
 }
 
 int Engine::load(int i, const void* buf, size_t size) {
-    if (i < 0 || i >= (int)lat.size() || !buf || size < sizeof(CkptHeader)) { set_error("bad checkpoint"); return LBM_EINVAL; }
+    if (!valid(i) || !buf || size < sizeof(CkptHeader)) { set_error("bad checkpoint"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     CkptHeader h;
     memcpy(&h, buf, sizeof h);

@@ -53,6 +53,7 @@ struct Lattice {
     int group = -1;
     int slot = -1;
     bool active = true;      // member of its group's work list
+    bool alive = true;       // false once removed (memory freed, index retired)
     // buffer b starts HEAD elements into its slot of the allocation; slots are
     // K * plane + TAIL elements (see engine.cu for why)
     static constexpr long long HEAD = 4, TAIL = 1024;
@@ -87,9 +88,17 @@ class Engine {
     Engine& operator=(const Engine&) = delete;
 
     int create(const lbm_spec* specs, int n, void* stream);
+    // dynamic membership (continuous batching): a lattice index stays valid
+    // until remove_lattice; removed indices are never reused
+    int open(void* stream);
+    int add_lattice(const lbm_spec* spec, int* index, bool upload = true);
+    int remove_lattice(int i);
+    static size_t footprint(const lbm_spec& s);  // device bytes of one lattice
+    bool dynamic_ = false;   // persistent grids sized for the machine, not the current work
     static int validate(const lbm_spec* in, lbm_spec* out);
 
     int n_lattices() const { return (int)lat.size(); }
+    bool valid(int i) const { return i >= 0 && i < (int)lat.size() && lat[i].alive; }
     Lattice& L(int i) { return lat[i]; }
     cudaStream_t stream() const { return stream_; }
 
@@ -112,6 +121,7 @@ class Engine {
     int record(int i, long long every, long long cap);
     int series(int i, lbm_obs* out, long long cap, long long* count);
     int set_budget(int i, long long steps);
+    int release_io(int i);   // free the staging buffer of init / readout
     int set_eps(int i, double eps);
     size_t checkpoint_size(int i) const;
     int save(int i, void* buf, size_t size);
@@ -137,6 +147,7 @@ class Engine {
     int readout(int i, double* f, double* rho, double* ux, double* uy, bool obs);
     LatDesc make_desc(const Lattice& L, const Group& g, int item_begin, double* partials) const;
     void invalidate_graph();
+    void free_lattice(Lattice& L);
 
     std::vector<Lattice> lat;
     std::vector<Group> groups;

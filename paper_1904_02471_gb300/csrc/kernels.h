@@ -20,7 +20,7 @@ struct GroupDev {
 // variants are the warp-specialised bulk-copy kernel (W columns x RB rows).
 // FD: TX x TY cells per tile, one cell per thread.
 enum CsTile { CS_T128x1 = 0, CS_T128x2, CS_T256x1, CS_T256x2, CS_T64x4, CS_B256x32, CS_B128x32, CS_NTILES };
-enum FdTile { FD_T32x8 = 0, FD_T32x4, FD_T64x4, FD_T32x16, FD_NTILES };
+enum FdTile { FD_T32x8 = 0, FD_T32x4, FD_T32x16, FD_T32x2, FD_NTILES };
 
 int cs_tile_tx(int v);
 int cs_tile_ty(int v);

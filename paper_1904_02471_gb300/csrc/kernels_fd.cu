@@ -25,6 +25,8 @@
 // buf[2] = f^(2). Storage offset as in the CS kernel (deviation form for
 // FP32, full f for FP64): WENO differences and the stage combination are
 // unchanged by the constant offset w_k rho0.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace lbm {
@@ -47,6 +49,45 @@ __constant__ float c_wt_f[3][5] = {
     {(float)GH<4>::w(0), (float)GH<4>::w(1), (float)GH<4>::w(2), (float)GH<4>::w(3), 0.f},
     {(float)GH<5>::w(0), (float)GH<5>::w(1), (float)GH<5>::w(2), (float)GH<5>::w(3), (float)GH<5>::w(4)}};
 
+// Per-population tables (v_kx, v_ky, w_k), indexed [q1 - 3][k] for
+// k = ix + q1 * iy, so the kernels never divide by a run-time q1.
+#define LBM_KV(Q, k, F) ((k) < (Q) * (Q) ? F<Q>(k) : 0.0)
+#define LBM_KROW(Q, F)                                                                                                  \
+    {LBM_KV(Q, 0, F), LBM_KV(Q, 1, F), LBM_KV(Q, 2, F), LBM_KV(Q, 3, F), LBM_KV(Q, 4, F), LBM_KV(Q, 5, F),         \
+     LBM_KV(Q, 6, F), LBM_KV(Q, 7, F), LBM_KV(Q, 8, F), LBM_KV(Q, 9, F), LBM_KV(Q, 10, F), LBM_KV(Q, 11, F),       \
+     LBM_KV(Q, 12, F), LBM_KV(Q, 13, F), LBM_KV(Q, 14, F), LBM_KV(Q, 15, F), LBM_KV(Q, 16, F), LBM_KV(Q, 17, F),   \
+     LBM_KV(Q, 18, F), LBM_KV(Q, 19, F), LBM_KV(Q, 20, F), LBM_KV(Q, 21, F), LBM_KV(Q, 22, F), LBM_KV(Q, 23, F),   \
+     LBM_KV(Q, 24, F)}
+__constant__ double c_kvx_d[3][25] = {LBM_KROW(3, vx_of), LBM_KROW(4, vx_of), LBM_KROW(5, vx_of)};
+__constant__ double c_kvy_d[3][25] = {LBM_KROW(3, vy_of), LBM_KROW(4, vy_of), LBM_KROW(5, vy_of)};
+__constant__ double c_kw_d[3][25] = {LBM_KROW(3, w_of), LBM_KROW(4, w_of), LBM_KROW(5, w_of)};
+#define LBM_KROWF(Q, F)                                                                                                 \
+    {(float)LBM_KV(Q, 0, F), (float)LBM_KV(Q, 1, F), (float)LBM_KV(Q, 2, F), (float)LBM_KV(Q, 3, F),               \
+     (float)LBM_KV(Q, 4, F), (float)LBM_KV(Q, 5, F), (float)LBM_KV(Q, 6, F), (float)LBM_KV(Q, 7, F),               \
+     (float)LBM_KV(Q, 8, F), (float)LBM_KV(Q, 9, F), (float)LBM_KV(Q, 10, F), (float)LBM_KV(Q, 11, F),             \
+     (float)LBM_KV(Q, 12, F), (float)LBM_KV(Q, 13, F), (float)LBM_KV(Q, 14, F), (float)LBM_KV(Q, 15, F),           \
+     (float)LBM_KV(Q, 16, F), (float)LBM_KV(Q, 17, F), (float)LBM_KV(Q, 18, F), (float)LBM_KV(Q, 19, F),           \
+     (float)LBM_KV(Q, 20, F), (float)LBM_KV(Q, 21, F), (float)LBM_KV(Q, 22, F), (float)LBM_KV(Q, 23, F),           \
+     (float)LBM_KV(Q, 24, F)}
+__constant__ float c_kvx_f[3][25] = {LBM_KROWF(3, vx_of), LBM_KROWF(4, vx_of), LBM_KROWF(5, vx_of)};
+__constant__ float c_kvy_f[3][25] = {LBM_KROWF(3, vy_of), LBM_KROWF(4, vy_of), LBM_KROWF(5, vy_of)};
+__constant__ float c_kw_f[3][25] = {LBM_KROWF(3, w_of), LBM_KROWF(4, w_of), LBM_KROWF(5, w_of)};
+
+template <typename T>
+struct KTab;
+template <>
+struct KTab<double> {
+    static __device__ __forceinline__ double vx(int q1, int k) { return c_kvx_d[q1 - 3][k]; }
+    static __device__ __forceinline__ double vy(int q1, int k) { return c_kvy_d[q1 - 3][k]; }
+    static __device__ __forceinline__ double w(int q1, int k) { return c_kw_d[q1 - 3][k]; }
+};
+template <>
+struct KTab<float> {
+    static __device__ __forceinline__ float vx(int q1, int k) { return c_kvx_f[q1 - 3][k]; }
+    static __device__ __forceinline__ float vy(int q1, int k) { return c_kvy_f[q1 - 3][k]; }
+    static __device__ __forceinline__ float w(int q1, int k) { return c_kw_f[q1 - 3][k]; }
+};
+
 template <typename T>
 __device__ __forceinline__ T node1(int q1, int i);
 template <>
@@ -60,32 +101,70 @@ __device__ __forceinline__ double wt1<double>(int q1, int i) { return c_wt_d[q1 
 template <>
 __device__ __forceinline__ float wt1<float>(int q1, int i) { return c_wt_f[q1 - 3][i]; }
 
-// WENO-5 interface value from the upwind-ordered stencil (a, b, c, d, e) =
-// (f_{i-2}, f_{i-1}, f_i, f_{i+1}, f_{i+2}) for the face i+1/2.
-// Candidates q_r on {i-2..i}, {i-1..i+1}, {i..i+2}; smoothness indicators
-// beta_r; nonlinear weights alpha_r = d_r / (eps + beta_r)^2 with linear
-// weights d = (1/10, 6/10, 3/10). The normalisation sum_r alpha_r q_r /
-// sum_r alpha_r is evaluated after multiplying numerator and denominator by
-// s0 s1 s2 (s_r = (eps + beta_r)^2), which needs one division instead of four.
+// Pairs of values evaluated together: the x-face and the y-face of a node
+// are two independent WENO-5 reconstructions, computed side by side. For
+// float they map to the packed FP32x2 instructions of sm_100+ (one
+// instruction, two results); for double they are two scalar operations.
 template <typename T>
-__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps) {
-    const T q0 = (T(2) * a - T(7) * b + T(11) * c) * T(1.0 / 6.0);
-    const T q1 = (-b + T(5) * c + T(2) * d) * T(1.0 / 6.0);
-    const T q2 = (T(2) * c + T(5) * d - e) * T(1.0 / 6.0);
-    T t0 = a - T(2) * b + c, u0 = a - T(4) * b + T(3) * c;
-    T t1 = b - T(2) * c + d, u1 = b - d;
-    T t2 = c - T(2) * d + e, u2 = T(3) * c - T(4) * d + e;
-    const T b0 = T(13.0 / 12.0) * t0 * t0 + T(0.25) * u0 * u0;
-    const T b1 = T(13.0 / 12.0) * t1 * t1 + T(0.25) * u1 * u1;
-    const T b2 = T(13.0 / 12.0) * t2 * t2 + T(0.25) * u2 * u2;
-    T s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
-    s0 *= s0;
-    s1 *= s1;
-    s2 *= s2;
-    const T a0 = T(0.1) * (s1 * s2);
-    const T a1 = T(0.6) * (s0 * s2);
-    const T a2 = T(0.3) * (s0 * s1);
-    return fdiv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+struct Pr;
+
+template <>
+struct Pr<float> {
+    using V = float2;
+    static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ V sp(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V div(V a, V b) { return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y)); }
+};
+
+template <>
+struct Pr<double> {
+    using V = double2;
+    static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ V sp(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+    static __device__ __forceinline__ V div(V a, V b) { return make_double2(a.x / b.x, a.y / b.y); }
+};
+
+// WENO-5 interface values (Jiang-Shu) of two faces at once, from their
+// upwind-ordered stencils (a, b, c, d, e) = (f_{i-2}, f_{i-1}, f_i, f_{i+1},
+// f_{i+2}) for the face i+1/2:
+//   candidates q0 = (2a - 7b + 11c)/6, q1 = (-b + 5c + 2d)/6, q2 = (2c + 5d - e)/6,
+//   smoothness beta_r = 13/12 (second difference)^2 + 1/4 (first difference)^2,
+//   weights alpha_r = d_r / (eps + beta_r)^2, d = (1/10, 6/10, 3/10),
+//   face = sum alpha_r q_r / sum alpha_r.
+// The linear weights are folded into the candidate coefficients, and numerator
+// and denominator are multiplied by s0 s1 s2 (s_r = (eps + beta_r)^2), so a
+// face costs one division.
+template <typename T>
+__device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typename Pr<T>::V b, typename Pr<T>::V c,
+                                                        typename Pr<T>::V d, typename Pr<T>::V e, typename Pr<T>::V eps) {
+    using P = Pr<T>;
+    using V = typename P::V;
+    const V q0 = P::fma(c, P::sp(T(11.0 / 60.0)), P::fma(b, P::sp(T(-7.0 / 60.0)), P::mul(a, P::sp(T(1.0 / 30.0)))));
+    const V q1 = P::fma(d, P::sp(T(1.0 / 5.0)), P::fma(c, P::sp(T(0.5)), P::mul(b, P::sp(T(-0.1)))));
+    const V q2 = P::fma(e, P::sp(T(-1.0 / 20.0)), P::fma(d, P::sp(T(0.25)), P::mul(c, P::sp(T(0.1)))));
+    const V t0 = P::add(P::fma(b, P::sp(T(-2)), a), c);
+    const V u0 = P::fma(c, P::sp(T(3)), P::fma(b, P::sp(T(-4)), a));
+    const V t1 = P::add(P::fma(c, P::sp(T(-2)), b), d);
+    const V u1 = P::fma(d, P::sp(T(-1)), b);
+    const V t2 = P::add(P::fma(d, P::sp(T(-2)), c), e);
+    const V u2 = P::fma(c, P::sp(T(3)), P::fma(d, P::sp(T(-4)), e));
+    const V k13 = P::sp(T(13.0 / 12.0)), k14 = P::sp(T(0.25));
+    V s0 = P::add(eps, P::fma(P::mul(t0, k13), t0, P::mul(P::mul(u0, u0), k14)));
+    V s1 = P::add(eps, P::fma(P::mul(t1, k13), t1, P::mul(P::mul(u1, u1), k14)));
+    V s2 = P::add(eps, P::fma(P::mul(t2, k13), t2, P::mul(P::mul(u2, u2), k14)));
+    s0 = P::mul(s0, s0);
+    s1 = P::mul(s1, s1);
+    s2 = P::mul(s2, s2);
+    const V p12 = P::mul(s1, s2), p02 = P::mul(s0, s2), p01 = P::mul(s0, s1);
+    const V num = P::fma(q2, p01, P::fma(q1, p02, P::mul(q0, p12)));
+    const V den = P::fma(p01, P::sp(T(0.3)), P::fma(p02, P::sp(T(0.6)), P::mul(p12, P::sp(T(0.1)))));
+    return P::div(num, den);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -93,35 +172,59 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-// Shared memory of one block: the K halo tiles of the stage input, two face
-// buffers (double-buffered across populations) and the reduction scratch.
-template <typename T, int TX, int TY>
+// Tile geometry: TX = 32 nodes along x (one warp per row), TY rows. The
+// staged halo tile of a population has HY = TY + 6 rows of HXP = 40 values,
+// columns x0 - 4 .. x0 + 35 (16-byte aligned rows; the stencil needs
+// x0 - 3 .. x0 + 34), rows y0 - 3 .. y0 + TY + 2.
+constexpr int FD_TX = 32;
+constexpr int FD_HXP = 40;
+
+template <typename T, int TY>
 __host__ __device__ constexpr size_t fd_smem_bytes(int K) {
-    return sizeof(T) * ((size_t)K * (TX + 6) * (TY + 6) + 2 * ((TX + 1) * TY + TX * (TY + 1))) +
-           sizeof(double) * (TX * TY / 32) * NOBS;
+    return sizeof(T) * ((size_t)K * (TY + 6) * FD_HXP + 2 * ((FD_TX + 1) * TY + FD_TX * (TY + 1))) +
+           sizeof(double) * (FD_TX * TY / 32) * NOBS;
 }
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) fd_stage_kernel(GroupDev g, int q1, int j, int stage) {
+// Resident blocks per SM the register allocation is bounded for: 1024
+// threads per SM for FP32, i.e. at most 64 registers per thread (shared
+// memory, about 40 KiB per 256-thread block for 16 populations, allows as
+// many); 512 threads (128 registers) for FP64.
+template <typename T, int TY>
+constexpr int fd_min_blocks() { return (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) > 0 ? (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) : 1; }
+
+template <typename T, int Q1, int TY>
+__global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_kernel(GroupDev g, int j, int stage) {
+    using P = Pr<T>;
+    using V = typename P::V;
+    constexpr int K = Q1 * Q1;
+    constexpr int TX = FD_TX, HXP = FD_HXP;
     constexpr int NT = TX * TY;
-    constexpr int HX = TX + 6, HY = TY + 6, HXY = HX * HY;
-    constexpr int NFX = (TX + 1) * TY;   // faces normal to x
-    constexpr int NFY = TX * (TY + 1);   // faces normal to y
+    constexpr int HY = TY + 6, HXY = HY * HXP;
+    constexpr int NFX = (TX + 1) * TY;   // faces normal to x: [TY][TX + 1]
+    constexpr int NFY = TX * (TY + 1);   // faces normal to y: [TY + 1][TX]
     constexpr int NF = NFX + NFY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int K = q1 * q1;
-    T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HX]
+    T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
     T* faces = tiles + (size_t)K * HXY;                  // [2][NF]
     double* red = reinterpret_cast<double*>(faces + 2 * NF);
 
     const int n_lat = g.hdr[0];
     const int total = g.hdr[1];
-    const int tid = threadIdx.y * TX + threadIdx.x;
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
     const int in_idx = stage == 1 ? 0 : (stage == 2 ? 1 : 2);
     const int out_idx = stage == 1 ? 1 : (stage == 2 ? 2 : 0);
     const T ca = stage == 1 ? T(0) : (stage == 2 ? T(0.75) : T(1.0 / 3.0));
     const T cb = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : T(2.0 / 3.0));
+    // warp 0 also evaluates the faces on the tile's right and top edges:
+    // lane l < TY: x-face right of node (TX-1, l); every lane: y-face above (l, TY-1)
+    const int ex_row = tx < TY ? tx : TY - 1;
+    // per-thread bases in the staged tile (all stencil offsets are immediates)
+    const int cidx = (ty + 3) * HXP + tx + 4;           // the node itself
+    const int xrow = (ty + 3) * HXP + tx;                // row of the node, column tx
+    const int ycol = ty * HXP + tx + 4;                  // column of the node, row ty
+    const int exrow = (ex_row + 3) * HXP + TX;           // extra x-face: virtual node (TX, ex_row)
+    const int eycol = TY * HXP + tx + 4;                 // extra y-face: virtual node (tx, TY)
 
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int li = find_lattice(g.item_begin, n_lat, item);
@@ -140,43 +243,44 @@ __global__ void __launch_bounds__(TX* TY) fd_stage_kernel(GroupDev g, int q1, in
         const T r0 = (T)dp->rho0;
         const T cdx = (T)dp->cdx;
         const T dtt = (T)dp->dt_tau;
-        const T eps = (T)dp->eps;
+        const V eps = P::sp((T)dp->eps);
         const long long cell = (long long)y * pitch + x;
-        const bool interior = x0 >= 3 && x0 + TX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+        const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
 
-        // 1. stage all K halo tiles of the stage input (periodic halo of 3)
-        __syncthreads();  // previous item finished reading the tiles
+        // 1. stage all K halo tiles of the stage input
+        __syncthreads();  // the previous item is done with the tiles
         if (interior) {
-            const T* src = U + (long long)(y0 - 3) * pitch + (x0 - 3);
-            for (int k = 0; k < K; ++k) {
-                const T* sk = src + k * plane;
-                T* dk = tiles + k * HXY;
-                for (int i = tid; i < HXY; i += NT) {
-                    const int r = i / HX, c = i - r * HX;
-                    dk[i] = sk[(long long)r * pitch + c];
-                }
+            // rows are 16-byte aligned: x0 - 4 is a multiple of 4, pitch of 32
+            constexpr int VEC = 16 / sizeof(T);
+            constexpr int RV = HXP / VEC;
+            using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            const T* src = U + (long long)(y0 - 3) * pitch + (x0 - 4);
+            for (int i = tid; i < K * HY * RV; i += NT) {
+                const int k = i / (HY * RV), rem = i - k * (HY * RV);
+                const int r = rem / RV, c = rem - r * RV;
+                const VT v = *reinterpret_cast<const VT*>(src + k * plane + (long long)r * pitch + c * VEC);
+                *reinterpret_cast<VT*>(tiles + (size_t)k * HXY + r * HXP + c * VEC) = v;
             }
         } else {
-            for (int k = 0; k < K; ++k) {
-                const T* sk = U + k * plane;
-                T* dk = tiles + k * HXY;
-                for (int i = tid; i < HXY; i += NT) {
-                    const int r = i / HX, c = i - r * HX;
-                    dk[i] = sk[(long long)wrapi(y0 - 3 + r, ny) * pitch + wrapi(x0 - 3 + c, nx)];
-                }
+            for (int i = tid; i < K * HXY; i += NT) {
+                const int k = i / HXY, rem = i - k * HXY;
+                const int r = rem / HXP, c = rem - r * HXP;
+                tiles[i] = U[k * plane + (long long)wrapi(y0 - 3 + r, ny) * pitch + wrapi(x0 - 4 + c, nx)];
             }
         }
-        T fn_next = (stage != 1 && active) ? Fn[cell] : T(0);
+        const T* __restrict__ fnp = Fn + cell;
+        T* __restrict__ op = out + cell;
+        T fn_next = (stage != 1 && active) ? fnp[0] : T(0);
         __syncthreads();
 
         // 2. moments of the stage input at this node, Eq. (f_moments_discrete)
-        const int cidx = (ty + 3) * HX + tx + 3;
         T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             const T u = tiles[k * HXY + cidx];
             dr += u;
-            jx += u * node1<T>(q1, k % q1);
-            jy += u * node1<T>(q1, k / q1);
+            if (vx_of<Q1>(k) != 0.0) jx += u * (T)vx_of<Q1>(k);
+            if (vy_of<Q1>(k) != 0.0) jy += u * (T)vy_of<Q1>(k);
         }
         const T rho = r0 + dr;
         const T inv = active ? T(1) / rho : T(0);
@@ -205,76 +309,81 @@ __global__ void __launch_bounds__(TX* TY) fd_stage_kernel(GroupDev g, int q1, in
             block_reduce_obs<T, NT>(acc, dp->partials + (long long)local * NOBS, red);
         }
 
-        // 3. per population: interface values, then the node update
+        // 3. per population: the node's x- and y-face values (one pair),
+        //    then the node update from the four faces around it
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             const T* tk = tiles + k * HXY;
-            T* fx = faces + (k & 1) * NF;
-            T* fy = fx + NFX;
-            const T vx = node1<T>(q1, k % q1), vy = node1<T>(q1, k / q1);
-            // Upwind stencil of a face, as (first point, step) in the tile:
-            // v > 0: f_{i-2..i+2} (first = left node - 2, step +1);
-            // v < 0: f_{i+3..i-1} (first = left node + 3, step -1); the same
-            // with rows (step +-HX) for faces normal to y.
-            const int ox = vx > T(0) ? -2 : 3, sx = vx > T(0) ? 1 : -1;
-            const int oy = vy > T(0) ? -2 * HX : 3 * HX, sy = vy > T(0) ? HX : -HX;
-            const int fbeg = vx == T(0) ? NFX : 0;
-            const int fend = vy == T(0) ? NFX : NF;
-            for (int f = fbeg + tid; f < fend; f += NT) {
-                const T* t;
-                int st;
-                if (f < NFX) {
-                    const int row = f / (TX + 1), col = f - row * (TX + 1);
-                    t = tk + (row + 3) * HX + (col + 2) + ox;  // left node of the face, shifted
-                    st = sx;
-                } else {
-                    const int f2 = f - NFX;
-                    const int row = f2 / TX, col = f2 - row * TX;
-                    t = tk + (row + 2) * HX + (col + 3) + oy;  // lower node of the face, shifted
-                    st = sy;
-                }
-                fx[f] = weno5<T>(t[0], t[st], t[2 * st], t[3 * st], t[4 * st], eps);
+            T* fx = faces + (k & 1) * NF;   // [TY][TX + 1]
+            T* fy = fx + NFX;               // [TY + 1][TX]
+            const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
+            // upwind stencil of the face on the low side of node (c, r):
+            // x, v > 0: cols c+1..c+5 of row r+3; v < 0: cols c+6..c+2
+            // y, v > 0: rows r..r+4 of col c+4; v < 0: rows r+5..r+1
+            const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
+            const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
+            {
+                const T* px = tk + xrow + xo;
+                const T* py = tk + ycol + yo;
+                const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                          P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                fx[ty * (TX + 1) + tx] = f.x;
+                fy[ty * TX + tx] = f.y;
+            }
+            if (ty == 0) {
+                const T* px = tk + exrow + xo;
+                const T* py = tk + eycol + yo;
+                const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                          P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
+                fy[TY * TX + tx] = f.y;
             }
             const T fn = fn_next;
-            if (stage != 1 && active && k + 1 < K) fn_next = Fn[(k + 1) * plane + cell];
+            if (stage != 1 && active && k + 1 < K) fn_next = fnp[(k + 1) * plane];
             __syncthreads();
             if (active) {
+                const T vx = (T)vxd, vy = (T)vyd;
                 T adv = T(0);
-                if (vx != T(0)) adv -= (vx * cdx) * (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]);
-                if (vy != T(0)) adv -= (vy * cdx) * (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]);
+                if (vxd != 0.0) adv -= (vx * cdx) * (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]);
+                if (vyd != 0.0) adv -= (vy * cdx) * (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]);
                 const T uk = tk[cidx];
                 const T xi = vx * ux + vy * uy;
-                const T wk = wt1<T>(q1, k % q1) * wt1<T>(q1, k / q1);
-                const T geq = wk * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                const T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
                 const T upd = uk + (adv - (uk - geq) * dtt);
-                out[k * plane + cell] = stage == 1 ? upd : ca * fn + cb * upd;
+                op[k * plane] = stage == 1 ? upd : ca * fn + cb * upd;
             }
         }
     }
 }
 
-int fd_tile_tx(int v) {
-    switch (v) {
-        case FD_T32x8: case FD_T32x4: case FD_T32x16: return 32;
-        case FD_T64x4: return 64;
-    }
-    return 0;
-}
+int fd_tile_tx(int v) { return (v >= 0 && v < FD_NTILES) ? FD_TX : 0; }
 int fd_tile_ty(int v) {
     switch (v) {
         case FD_T32x8: return 8;
-        case FD_T32x4: case FD_T64x4: return 4;
+        case FD_T32x4: return 4;
         case FD_T32x16: return 16;
+        case FD_T32x2: return 2;
     }
     return 0;
 }
 
-template <typename T>
-static const void* fd_kernel_ptr(int tile) {
+template <typename T, int Q1>
+static const void* fd_kernel_ptr_q(int tile) {
     switch (tile) {
-        case FD_T32x8: return (const void*)fd_stage_kernel<T, 32, 8>;
-        case FD_T32x4: return (const void*)fd_stage_kernel<T, 32, 4>;
-        case FD_T64x4: return (const void*)fd_stage_kernel<T, 64, 4>;
-        case FD_T32x16: return (const void*)fd_stage_kernel<T, 32, 16>;
+        case FD_T32x8: return (const void*)fd_stage_kernel<T, Q1, 8>;
+        case FD_T32x4: return (const void*)fd_stage_kernel<T, Q1, 4>;
+        case FD_T32x16: return (const void*)fd_stage_kernel<T, Q1, 16>;
+        case FD_T32x2: return (const void*)fd_stage_kernel<T, Q1, 2>;
+    }
+    return nullptr;
+}
+
+template <typename T>
+static const void* fd_kernel_ptr(int tile, int q1) {
+    switch (q1) {
+        case 3: return fd_kernel_ptr_q<T, 3>(tile);
+        case 4: return fd_kernel_ptr_q<T, 4>(tile);
+        case 5: return fd_kernel_ptr_q<T, 5>(tile);
     }
     return nullptr;
 }
@@ -282,30 +391,30 @@ static const void* fd_kernel_ptr(int tile) {
 template <typename T>
 static size_t fd_smem(int tile, int K) {
     switch (tile) {
-        case FD_T32x8: return fd_smem_bytes<T, 32, 8>(K);
-        case FD_T32x4: return fd_smem_bytes<T, 32, 4>(K);
-        case FD_T64x4: return fd_smem_bytes<T, 64, 4>(K);
-        case FD_T32x16: return fd_smem_bytes<T, 32, 16>(K);
+        case FD_T32x8: return fd_smem_bytes<T, 8>(K);
+        case FD_T32x4: return fd_smem_bytes<T, 4>(K);
+        case FD_T32x16: return fd_smem_bytes<T, 16>(K);
+        case FD_T32x2: return fd_smem_bytes<T, 2>(K);
     }
     return 0;
 }
 
-static const void* fd_fn(int precision, int tile) {
-    return precision == LBM_FP64 ? fd_kernel_ptr<double>(tile) : fd_kernel_ptr<float>(tile);
+static const void* fd_fn(int precision, int tile, int q1) {
+    return precision == LBM_FP64 ? fd_kernel_ptr<double>(tile, q1) : fd_kernel_ptr<float>(tile, q1);
 }
 static size_t fd_bytes(int precision, int tile, int q1) {
     return precision == LBM_FP64 ? fd_smem<double>(tile, q1 * q1) : fd_smem<float>(tile, q1 * q1);
 }
 
-// Opt every variant into the largest dynamic shared memory it can need (25
-// populations); done once per process.
-static cudaError_t fd_prepare(int precision, int tile) {
-    static bool done[2][FD_NTILES] = {};
+// Opt each variant into the dynamic shared memory it needs; once per process.
+static cudaError_t fd_prepare(int precision, int tile, int q1) {
+    static bool done[2][FD_NTILES][3] = {};
     const int p = precision == LBM_FP64 ? 0 : 1;
-    if (done[p][tile]) return cudaSuccess;
-    const size_t need = fd_bytes(precision, tile, 5);
-    cudaError_t e = cudaFuncSetAttribute(fd_fn(precision, tile), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-    if (e == cudaSuccess) done[p][tile] = true;
+    if (done[p][tile][q1 - 3]) return cudaSuccess;
+    const size_t need = fd_bytes(precision, tile, q1);
+    cudaError_t e = cudaFuncSetAttribute(fd_fn(precision, tile, q1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)need);
+    if (e == cudaSuccess) done[p][tile][q1 - 3] = true;
     return e;
 }
 
@@ -313,19 +422,19 @@ cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const Gro
                             cudaStream_t s) {
     if (tile < 0 || tile >= FD_NTILES || grid <= 0 || q1 < 3 || q1 > 5 || stage < 1 || stage > 3)
         return cudaErrorInvalidValue;
-    const void* fn = fd_fn(precision, tile);
-    cudaError_t e = fd_prepare(precision, tile);
+    const void* fn = fd_fn(precision, tile, q1);
+    cudaError_t e = fd_prepare(precision, tile, q1);
     if (e != cudaSuccess) return e;
     GroupDev gg = g;
-    int qq = q1, jj = j, ss = stage;
-    void* args[] = {&gg, &qq, &jj, &ss};
+    int jj = j, ss = stage;
+    void* args[] = {&gg, &jj, &ss};
     return cudaLaunchKernel(fn, dim3(grid), dim3(fd_tile_tx(tile), fd_tile_ty(tile)), args, fd_bytes(precision, tile, q1), s);
 }
 
 int fd_blocks_per_sm(int precision, int q1, int tile) {
-    if (tile < 0 || tile >= FD_NTILES || fd_prepare(precision, tile) != cudaSuccess) return 1;
+    if (tile < 0 || tile >= FD_NTILES || q1 < 3 || q1 > 5 || fd_prepare(precision, tile, q1) != cudaSuccess) return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile), fd_tile_tx(tile) * fd_tile_ty(tile),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile, q1), fd_tile_tx(tile) * fd_tile_ty(tile),
                                                       fd_bytes(precision, tile, q1)) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;

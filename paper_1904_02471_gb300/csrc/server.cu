@@ -1,0 +1,370 @@
+// Continuous-batching run server.
+//
+// Requests are complete runs (model, lattice, tau, steps, initial state).
+// One worker thread owns a dynamic Engine: it admits queued requests as
+// slots and device memory (an HBM budget on the summed lattice footprints)
+// free up, advances every resident run together in rounds of chunk_steps
+// (one captured CUDA-graph replay per 32 steps, runs that reach their step
+// budget are skipped by the kernels), and retires finished runs at the end of
+// a round: final observables, recorded series, fitted apparent viscosity,
+// then the lattice's memory is released and waiting requests are admitted.
+// Requests that arrive while others are on the GPU join at the next round,
+// so their work overlaps on the device.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Req {
+    lbm_request r{};
+    double t_submit = 0, t_admit = -1, t_done = -1;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int lat = -1;
+    size_t bytes = 0;
+    bool cancel = false;
+    lbm_result res{};
+    std::vector<lbm_obs> series;
+};
+
+// Initial fields of a request (Sec. 4.1-4.3 set-ups), node coordinates
+// x_i = i, one wavelength across the lattice.
+void initial_fields(const lbm_request& q, std::vector<double>& rho, std::vector<double>& ux, std::vector<double>& uy) {
+    const int nx = q.spec.nx, ny = q.spec.ny;
+    const size_t n = (size_t)nx * ny;
+    rho.assign(n, 1.0);
+    ux.assign(n, 0.0);
+    uy.assign(n, 0.0);
+    const double rho0 = q.spec.rho0 > 0 ? q.spec.rho0 : 1.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t c = (size_t)y * nx + x;
+            const double kx = 2 * kPi * x / nx, ky = 2 * kPi * y / ny;
+            if (q.init == 0) {  // Taylor-Green, pressure-balanced density (cs = 1)
+                ux[c] = q.U * std::sin(kx) * std::cos(ky);
+                uy[c] = -q.U * std::cos(kx) * std::sin(ky);
+                rho[c] = rho0 * (1.0 + q.U * q.U / 4.0 * (std::cos(2 * kx) + std::cos(2 * ky)));
+            } else if (q.init == 1) {  // shear wave
+                rho[c] = rho0;
+                uy[c] = q.U * std::sin(kx);
+            } else {  // shock tube
+                rho[c] = x <= nx / 2 ? q.rho_l : q.rho_r;
+            }
+        }
+}
+
+}  // namespace
+
+struct lbm_server {
+    lbm::Engine e;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    size_t budget = 0, resident = 0;
+    int max_slots = 1, chunk = 256;
+    uint64_t next_ticket = 1;
+    std::map<uint64_t, Req> reqs;
+    std::deque<uint64_t> queue;
+    std::vector<uint64_t> running;
+    int64_t n_done = 0;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+
+    void finish(Req& q, int status) {  // caller holds mu
+        q.state = 2;
+        q.t_done = now();
+        q.res.status = status;
+        q.res.user_tag = q.r.user_tag;
+        q.res.t_submit = q.t_submit;
+        q.res.t_admit = q.t_admit;
+        q.res.t_done = q.t_done;
+        q.res.n_series = (int64_t)q.series.size();
+        ++n_done;
+        cv_done.notify_all();
+    }
+
+    // Set-up of an admitted request on the worker thread (no lock held).
+    int start(Req& q) {
+        int idx = -1;
+        int rc = e.add_lattice(&q.r.spec, &idx);
+        if (rc) return rc;
+        q.lat = idx;
+        std::vector<double> rho, ux, uy;
+        initial_fields(q.r, rho, ux, uy);
+        rc = e.init(idx, rho.data(), ux.data(), uy.data());
+        if (rc) return rc;
+        const int nx = q.r.spec.nx, ny = q.r.spec.ny;
+        if (q.r.init == 0 || q.r.init == 1) {
+            std::vector<double> px(nx), py(ny);
+            for (int x = 0; x < nx; ++x) px[x] = std::sin(2 * kPi * x / nx);
+            for (int y = 0; y < ny; ++y) py[y] = q.r.init == 0 ? std::cos(2 * kPi * y / ny) : 1.0;
+            rc = e.set_probe(idx, q.r.init == 0 ? 0 : 1, px.data(), py.data(),
+                             (q.r.init == 0 ? 4.0 : 2.0) / ((double)nx * ny));
+            if (rc) return rc;
+        }
+        rc = e.observables(idx, &q.res.first);
+        if (rc) return rc;
+        if (q.r.obs_every > 0) {
+            rc = e.record(idx, q.r.obs_every, q.r.steps / q.r.obs_every + 1);
+            if (rc) return rc;
+        }
+        rc = e.release_io(idx);  // only the state stays resident (the budget counts it)
+        if (rc) return rc;
+        return e.set_budget(idx, q.r.steps);
+    }
+
+    // Results of a run whose budget is exhausted (worker thread, no lock).
+    int collect(Req& q) {
+        int rc = e.observables(q.lat, &q.res.last);
+        if (rc) return rc;
+        q.res.steps = e.L(q.lat).step0;
+        if (q.r.obs_every > 0) {
+            long long n = 0;
+            rc = e.series(q.lat, nullptr, 0, &n);
+            if (rc) return rc;
+            q.series.resize((size_t)n);
+            if (n) rc = e.series(q.lat, q.series.data(), n, &n);
+            if (rc) return rc;
+        }
+        q.res.nu_fit = 0;
+        if ((q.r.init == 0 || q.r.init == 1) && q.series.size() >= 4) {
+            // decay of the projected amplitude, Eq. (shear_sol) / Eq. (taylor):
+            // A ~ exp(-m k^2 nu t), m = 1 (shear) or 2 (Taylor-Green)
+            std::vector<double> t, a;
+            for (const auto& o : q.series) {
+                t.push_back(o.time);
+                a.push_back(o.amp);
+            }
+            double gamma = 0, a0 = 0;
+            const double skip = 0.1 * t.back();
+            if (lbm_fit_decay(t.data(), a.data(), (int64_t)t.size(), skip, &gamma, &a0) == LBM_OK) {
+                const double L = q.r.spec.nx * e.L(q.lat).spec.dx;
+                const double k = 2 * kPi / L;
+                q.res.nu_fit = gamma / ((q.r.init == 0 ? 2.0 : 1.0) * k * k);
+            }
+        }
+        return q.res.last.nonfinite ? LBM_ENONFINITE : LBM_OK;
+    }
+
+    void loop() {
+        for (;;) {
+            std::vector<uint64_t> admit;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                for (;;) {
+                    // admission: oldest first, skipping requests that do not
+                    // fit yet (first fit over the queue)
+                    for (auto it = queue.begin(); it != queue.end();) {
+                        Req& q = reqs[*it];
+                        if ((int)(running.size() + admit.size()) >= max_slots) break;
+                        if (resident + q.bytes <= budget) {
+                            resident += q.bytes;
+                            q.state = 1;
+                            q.t_admit = now();
+                            admit.push_back(*it);
+                            it = queue.erase(it);
+                        } else {
+                            ++it;
+                        }
+                    }
+                    if (!admit.empty() || !running.empty() || stop) break;
+                    cv_work.wait(lk);
+                }
+                if (stop && admit.empty() && running.empty()) return;
+            }
+            for (uint64_t t : admit) {
+                Req* q;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    q = &reqs[t];
+                }
+                const int rc = start(*q);
+                std::lock_guard<std::mutex> lk(mu);
+                if (rc) {
+                    if (q->lat >= 0) e.remove_lattice(q->lat);
+                    resident -= q->bytes;
+                    finish(*q, rc);
+                } else {
+                    running.push_back(t);
+                }
+            }
+            if (running.empty()) continue;
+            int rc = e.step(chunk);
+            if (rc == LBM_OK) rc = e.sync();
+            std::vector<uint64_t> still;
+            for (uint64_t t : running) {
+                Req* q;
+                bool cancel;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    q = &reqs[t];
+                    cancel = q->cancel || stop;
+                }
+                const lbm::Lattice& L = e.L(q->lat);
+                if (rc == LBM_OK && !cancel && L.remaining > 0) {
+                    still.push_back(t);
+                    continue;
+                }
+                int st = rc;
+                if (st == LBM_OK && !cancel) st = collect(*q);
+                else if (st == LBM_OK) st = LBM_ECANCELLED;
+                e.remove_lattice(q->lat);
+                std::lock_guard<std::mutex> lk(mu);
+                resident -= q->bytes;
+                finish(*q, st);
+            }
+            running.swap(still);
+        }
+    }
+};
+
+extern "C" {
+
+int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, int chunk_steps, void* stream) {
+    try {
+        if (!out || hbm_budget_bytes == 0 || max_slots < 1 || chunk_steps < 1) {
+            lbm::set_error("server needs a budget, at least one slot and a positive chunk");
+            return LBM_EINVAL;
+        }
+        *out = nullptr;
+        lbm_server* s = new lbm_server;
+        s->e.dynamic_ = true;
+        const int rc = s->e.open(stream);
+        if (rc) {
+            delete s;
+            return rc;
+        }
+        s->budget = hbm_budget_bytes;
+        s->max_slots = max_slots;
+        s->chunk = chunk_steps;
+        s->worker = std::thread([s] { s->loop(); });
+        *out = s;
+        return LBM_OK;
+    } catch (...) {
+        lbm::set_error("server creation failed");
+        return LBM_ENOMEM;
+    }
+}
+
+int lbm_submit(lbm_server* s, const lbm_request* req, uint64_t* ticket) {
+    try {
+        if (!s || !req || !ticket) return LBM_EINVAL;
+        lbm_spec spec;
+        int rc = lbm::Engine::validate(&req->spec, &spec);
+        if (rc) return rc;
+        if (req->steps < 0 || req->init < 0 || req->init > 2 || req->obs_every < 0 || !std::isfinite(req->U) ||
+            (req->init == 2 && !(req->rho_l > 0 && req->rho_r > 0))) {
+            lbm::set_error("bad request (steps, init, obs_every, U or shock densities)");
+            return LBM_EINVAL;
+        }
+        const size_t bytes = lbm::Engine::footprint(spec);
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (bytes > s->budget) {
+            lbm::set_error("request can never fit the server's memory budget");
+            return LBM_ENOMEM;
+        }
+        const uint64_t t = s->next_ticket++;
+        Req& q = s->reqs[t];
+        q.r = *req;
+        q.r.spec = spec;
+        q.bytes = bytes;
+        q.t_submit = s->now();
+        s->queue.push_back(t);
+        *ticket = t;
+        s->cv_work.notify_one();
+        return LBM_OK;
+    } catch (...) {
+        lbm::set_error("submit failed");
+        return LBM_ENOMEM;
+    }
+}
+
+int lbm_poll(lbm_server* s, uint64_t ticket, lbm_result* out) {
+    if (!s || !out) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return LBM_ENOTFOUND;
+    if (it->second.state != 2) return LBM_ENOTREADY;
+    *out = it->second.res;
+    return LBM_OK;
+}
+
+int lbm_result_series(lbm_server* s, uint64_t ticket, lbm_obs* out, int64_t cap, int64_t* count) {
+    if (!s || cap < 0 || (cap > 0 && !out)) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return LBM_ENOTFOUND;
+    if (it->second.state != 2) return LBM_ENOTREADY;
+    const auto& v = it->second.series;
+    if (count) *count = (int64_t)v.size();
+    for (int64_t i = 0; i < cap && i < (int64_t)v.size(); ++i) out[i] = v[i];
+    return LBM_OK;
+}
+
+int lbm_cancel(lbm_server* s, uint64_t ticket) {
+    if (!s) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return LBM_ENOTFOUND;
+    Req& q = it->second;
+    if (q.state == 0) {
+        for (auto qi = s->queue.begin(); qi != s->queue.end(); ++qi)
+            if (*qi == ticket) {
+                s->queue.erase(qi);
+                break;
+            }
+        s->finish(q, LBM_ECANCELLED);
+    } else if (q.state == 1) {
+        q.cancel = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_server_drain(lbm_server* s, double timeout_s) {
+    if (!s) return LBM_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (s->n_done < (int64_t)s->reqs.size()) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->n_done < (int64_t)s->reqs.size()) {
+            lbm::set_error("drain timed out");
+            return LBM_ETIMEOUT;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* finished, size_t* resident_bytes) {
+    if (!s) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (queued) *queued = (int64_t)s->queue.size();
+    if (running) *running = (int64_t)s->reqs.size() - (int64_t)s->queue.size() - s->n_done;
+    if (finished) *finished = s->n_done;
+    if (resident_bytes) *resident_bytes = s->resident;
+    return LBM_OK;
+}
+
+void lbm_server_destroy(lbm_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        for (uint64_t t : s->queue) s->finish(s->reqs[t], LBM_ECANCELLED);
+        s->queue.clear();
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    delete s;
+}
+
+}  // extern "C"

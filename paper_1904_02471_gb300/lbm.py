@@ -44,6 +44,25 @@ class lbm_view(ctypes.Structure):
                 ("elem_bytes", ctypes.c_int32), ("cs_pull_phase", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class lbm_request(ctypes.Structure):
+    _fields_ = [("spec", lbm_spec), ("steps", ctypes.c_int64), ("init", ctypes.c_int), ("obs_every", ctypes.c_int),
+                ("U", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_r", ctypes.c_double),
+                ("user_tag", ctypes.c_uint64)]
+
+
+class lbm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("reserved", ctypes.c_int), ("user_tag", ctypes.c_uint64),
+                ("steps", ctypes.c_int64), ("first", lbm_obs), ("last", lbm_obs), ("nu_fit", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("n_series", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "first", "last")}
+        d["first"] = self.first.as_dict()
+        d["last"] = self.last.as_dict()
+        return d
+
+
 class LbmError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -112,6 +131,15 @@ _SIGS = [
     ("lbm_batch_kernel_launches", _i64, [_P]),
     ("lbm_kernel_launches", _i64, [_P]),
     ("lbm_batch_tune", _i, [_P, _i, ctypes.c_char_p, _sz]),
+    ("lbm_server_create", _i, [ctypes.POINTER(_P), _sz, _i, _i, _P]),
+    ("lbm_submit", _i, [_P, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("lbm_poll", _i, [_P, ctypes.c_uint64, ctypes.POINTER(lbm_result)]),
+    ("lbm_result_series", _i, [_P, ctypes.c_uint64, ctypes.POINTER(lbm_obs), _i64, ctypes.POINTER(_i64)]),
+    ("lbm_cancel", _i, [_P, ctypes.c_uint64]),
+    ("lbm_server_drain", _i, [_P, _d]),
+    ("lbm_server_stats", _i, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                              ctypes.POINTER(_sz)]),
+    ("lbm_server_destroy", None, [_P]),
     ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, _d, _i, _P, _P, _d, _i64, _d,
                                      _P, _P]),
 ]
@@ -449,3 +477,75 @@ class Batch:
         buf = ctypes.create_string_buffer(4096)
         check(lib().lbm_batch_tune(self._h, trial_steps, buf, 4096), "lbm_batch_tune")
         return buf.value.decode()
+
+
+INITS = {"tg": 0, "taylor_green": 0, "shear": 1, "shock": 2}
+
+
+def make_request(spec: lbm_spec, steps, init="tg", U=0.01, obs_every=0, rho_l=1.1, rho_r=0.9, tag=0) -> lbm_request:
+    r = lbm_request()
+    r.spec = spec
+    r.steps = int(steps)
+    r.init = INITS[init] if isinstance(init, str) else init
+    r.obs_every = int(obs_every)
+    r.U, r.rho_l, r.rho_r = U, rho_l, rho_r
+    r.user_tag = tag
+    return r
+
+
+class Server:
+    """Continuous-batching run server (lbm_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, chunk_steps=256, stream=None):
+        self._h = ctypes.c_void_p()
+        check(lib().lbm_server_create(ctypes.byref(self._h), int(hbm_budget_bytes), max_slots, chunk_steps,
+                                      _stream_ptr(stream)), "lbm_server_create")
+
+    def close(self):
+        if self._h:
+            lib().lbm_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, req: lbm_request) -> int:
+        t = ctypes.c_uint64()
+        check(lib().lbm_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "lbm_submit")
+        return t.value
+
+    def poll(self, ticket):
+        r = lbm_result()
+        rc = lib().lbm_poll(self._h, ticket, ctypes.byref(r))
+        if rc == LBM_ENOTREADY:
+            return None
+        check(rc, "lbm_poll")
+        return r.as_dict()
+
+    def series(self, ticket):
+        n = ctypes.c_int64()
+        check(lib().lbm_result_series(self._h, ticket, None, 0, ctypes.byref(n)), "lbm_result_series")
+        arr = (lbm_obs * max(n.value, 1))()
+        check(lib().lbm_result_series(self._h, ticket, arr, n.value, ctypes.byref(n)), "lbm_result_series")
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def cancel(self, ticket):
+        check(lib().lbm_cancel(self._h, ticket), "lbm_cancel")
+
+    def drain(self, timeout_s=600.0):
+        check(lib().lbm_server_drain(self._h, timeout_s), "lbm_server_drain")
+
+    def stats(self):
+        q, r, f, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        check(lib().lbm_server_stats(self._h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f), ctypes.byref(b)),
+              "lbm_server_stats")
+        return dict(queued=q.value, running=r.value, finished=f.value, resident_bytes=b.value)

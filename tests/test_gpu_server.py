@@ -1,0 +1,150 @@
+"""The continuous-batching run server (lbm_server_*) on the GPU.
+
+Each run gives the same result alone and in a mix of concurrent runs;
+admission follows the memory budget and the slot count; runs that arrive
+while others are on the GPU start before those finish; cancellation; and the
+fitted apparent viscosity of a shear wave matches Eq. (nulu).
+"""
+import math
+import time
+
+import pytest
+
+import paper_1904_02471_gb300 as pkg
+from paper_1904_02471_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+SQ3 = math.sqrt(3.0)
+GB = 1 << 30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1904_02471_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def _cs(n, tau, prec="fp32"):
+    return pkg.make_spec("cs", 3, n, n, tau, 0.0, 0.0, prec)
+
+
+def _fd(n, q, prec="fp32", tau_star=0.9):
+    # dt <= tau and a Courant number of 0.4 (CFL = 1 is unstable for
+    # WENO-5 + RK3 advection along both axes)
+    tau = pkg.lbm_tau_fd_from_lu(n, tau_star / SQ3)
+    dt = min(tau, 0.4 * pkg.lbm_fd_max_dt(q, 1.0 / n, 1e300))
+    return pkg.make_spec("fd", q, n, n, tau, dt, 0.0, prec)
+
+
+MIX = [
+    (lambda: _cs(64, 0.5), 300, "tg", 0.01 * SQ3),
+    (lambda: _fd(48, 4), 200, "tg", 0.01),
+    (lambda: _cs(96, 0.7, "fp64"), 450, "shear", 0.01 * SQ3),
+    (lambda: _fd(32, 5, "fp64"), 120, "tg", 0.01),
+    (lambda: _cs(40, 1.0), 600, "shear", 0.02 * SQ3),
+    (lambda: _fd(40, 4), 260, "shock", 0.0),
+    (lambda: _cs(128, 0.35), 100, "shock", 0.0),
+    (lambda: _fd(56, 4, "fp32", 1.4), 330, "tg", 0.01),
+]
+
+
+def _req(i):
+    spec_fn, steps, init, U = MIX[i]
+    return lbm.make_request(spec_fn(), steps, init, U, obs_every=10, rho_l=1.2, rho_r=0.8, tag=i)
+
+
+def _run(reqs, budget=8 * GB, slots=64, chunk=64):
+    with lbm.Server(budget, slots, chunk) as S:
+        tickets = [S.submit(r) for r in reqs]
+        S.drain(300)
+        return [(S.poll(t), S.series(t)) for t in tickets]
+
+
+def test_mix_equals_alone():
+    """Every run's final observables and series are the same whether it runs
+    alone or together with the others (4 slots, so some wait in the queue)."""
+    mixed = _run([_req(i) for i in range(len(MIX))], slots=4, chunk=48)
+    for i in range(len(MIX)):
+        (res_m, ser_m), = [mixed[i]]
+        (res_a, ser_a), = _run([_req(i)], chunk=48)
+        assert res_m["status"] == lbm.LBM_OK and res_a["status"] == lbm.LBM_OK, (i, res_m["status"])
+        assert res_m["user_tag"] == i and res_m["steps"] == MIX[i][1]
+        for key in ("mass", "mom_x", "mom_y", "amp"):
+            a, b = res_m["last"][key], res_a["last"][key]
+            assert abs(a - b) <= 1e-12 * max(1.0, abs(res_a["last"]["mass"]) if key != "amp" else abs(b)), (i, key, a, b)
+        assert len(ser_m) == len(ser_a) == MIX[i][1] // 10
+        for sm, sa in zip(ser_m, ser_a):
+            assert sm["step"] == sa["step"]
+            assert abs(sm["amp"] - sa["amp"]) <= 1e-12 * abs(sa["amp"]) + 1e-300
+
+
+def test_admission_follows_budget_and_slots():
+    spec = _cs(1024, 0.6)
+    one = 2 * 9 * 1056 * 1024 * 4  # about one lattice's state
+    with lbm.Server(int(1.5 * one) + (1 << 20), 8, 32) as S:
+        t1 = S.submit(lbm.make_request(spec, 400, "tg", 0.01))
+        t2 = S.submit(lbm.make_request(spec, 100, "tg", 0.01))
+        S.drain(300)
+        r1, r2 = S.poll(t1), S.poll(t2)
+    assert r1["status"] == r2["status"] == lbm.LBM_OK
+    assert r2["t_admit"] >= r1["t_done"] - 1e-3, (r1, r2)  # second waited for memory
+    with lbm.Server(1 << 20, 8, 32) as S:
+        with pytest.raises(lbm.LbmError) as ei:
+            S.submit(lbm.make_request(spec, 10, "tg", 0.01))
+        assert ei.value.code == lbm.LBM_ENOMEM
+
+
+def test_late_arrivals_overlap():
+    """A run submitted while a long run is on the GPU starts (and ends) before it."""
+    with lbm.Server(8 * GB, 8, 32) as S:
+        t_long = S.submit(lbm.make_request(_cs(512, 0.6), 4000, "tg", 0.01))
+        time.sleep(0.05)
+        t_short = S.submit(lbm.make_request(_fd(64, 4), 50, "tg", 0.01))
+        S.drain(300)
+        rl, rs = S.poll(t_long), S.poll(t_short)
+    assert rl["status"] == rs["status"] == lbm.LBM_OK
+    assert rs["t_admit"] < rl["t_done"] and rs["t_done"] < rl["t_done"]
+
+
+def test_cancel():
+    with lbm.Server(8 * GB, 1, 32) as S:
+        t1 = S.submit(lbm.make_request(_cs(256, 0.6), 200000, "tg", 0.01))
+        t2 = S.submit(lbm.make_request(_cs(256, 0.6), 10, "tg", 0.01))
+        time.sleep(0.2)
+        S.cancel(t2)  # still queued (one slot)
+        S.cancel(t1)  # running
+        S.drain(120)
+        assert S.poll(t2)["status"] == lbm.LBM_ECANCELLED
+        r1 = S.poll(t1)
+        assert r1["status"] == lbm.LBM_ECANCELLED and r1["steps"] < 200000
+        with pytest.raises(lbm.LbmError):
+            S.poll(12345)
+
+
+def test_unstable_run_is_reported_non_finite():
+    """A run that blows up (FD at CFL = 1 along both axes) finishes with
+    LBM_ENONFINITE instead of a silent NaN result; the others are unaffected."""
+    n, q = 56, 4
+    tau = pkg.lbm_tau_fd_from_lu(n, 1.4 / SQ3)
+    bad = pkg.make_spec("fd", q, n, n, tau, pkg.lbm_fd_max_dt(q, 1.0 / n, tau), 0.0, "fp32")
+    res = _run([lbm.make_request(bad, 330, "tg", 0.01), _req(0)])
+    assert res[0][0]["status"] == lbm.LBM_ENONFINITE
+    assert res[1][0]["status"] == lbm.LBM_OK
+
+
+def test_shear_wave_viscosity_fit():
+    """nu_fit of a CS shear wave is nu_LU = tau_LU - dt/2 (Eq. nulu) to within
+    the discretisation error of a 64-node wave."""
+    tau = 0.8 / SQ3
+    spec = pkg.make_spec("cs", 3, 64, 4, tau, 0.0, 0.0, "fp64")
+    with lbm.Server(GB, 4, 100) as S:
+        t = S.submit(lbm.make_request(spec, 2000, "shear", 0.01 * SQ3, obs_every=50))
+        S.drain(120)
+        r = S.poll(t)
+    nu = pkg.lbm_nu(lbm.LBM_CS, tau, 1 / SQ3)
+    assert r["status"] == lbm.LBM_OK
+    assert abs(r["nu_fit"] / nu - 1) < 2e-3, r["nu_fit"] / nu
