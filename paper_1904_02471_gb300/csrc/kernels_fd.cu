@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace lbm {
 
@@ -130,30 +131,36 @@ struct Pr<double> {
     static __device__ __forceinline__ V div(V a, V b) { return make_double2(a.x / b.x, a.y / b.y); }
 };
 
-// WENO-5 interface values (Jiang-Shu) of two faces at once, from their
+// WENO-5 interface values (Jiang-Shu) of two faces at once, as corrections
+// face - c to the upwind node value c (see below), from their
 // upwind-ordered stencils (a, b, c, d, e) = (f_{i-2}, f_{i-1}, f_i, f_{i+1},
 // f_{i+2}) for the face i+1/2:
 //   candidates q0 = (2a - 7b + 11c)/6, q1 = (-b + 5c + 2d)/6, q2 = (2c + 5d - e)/6,
 //   smoothness beta_r = 13/12 (second difference)^2 + 1/4 (first difference)^2,
 //   weights alpha_r = d_r / (eps + beta_r)^2, d = (1/10, 6/10, 3/10),
 //   face = sum alpha_r q_r / sum alpha_r.
-// The linear weights are folded into the candidate coefficients, and numerator
-// and denominator are multiplied by s0 s1 s2 (s_r = (eps + beta_r)^2), so a
-// face costs one division.
+// Numerator and denominator are multiplied by s0 s1 s2 (s_r = (eps +
+// beta_r)^2), so a face costs one division.
 template <typename T>
 __device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typename Pr<T>::V b, typename Pr<T>::V c,
                                                         typename Pr<T>::V d, typename Pr<T>::V e, typename Pr<T>::V eps) {
     using P = Pr<T>;
     using V = typename P::V;
-    const V q0 = P::fma(c, P::sp(T(11.0 / 60.0)), P::fma(b, P::sp(T(-7.0 / 60.0)), P::mul(a, P::sp(T(1.0 / 30.0)))));
-    const V q1 = P::fma(d, P::sp(T(1.0 / 5.0)), P::fma(c, P::sp(T(0.5)), P::mul(b, P::sp(T(-0.1)))));
-    const V q2 = P::fma(e, P::sp(T(-1.0 / 20.0)), P::fma(d, P::sp(T(0.25)), P::mul(c, P::sp(T(0.1)))));
+    // second differences t_r and one-sided / central first differences u_r of
+    // the three stencils; the candidates follow from them:
+    // q0 = c + t0/12 + u0/4, q1 = c + t1/12 - u1/4, q2 = c + t2/12 - u2/4.
+    // The function returns face - c, the correction to the upwind node value
+    // c: a small number, so its rounding error is small next to the flux
+    // differences it feeds (see the node update).
     const V t0 = P::add(P::fma(b, P::sp(T(-2)), a), c);
     const V u0 = P::fma(c, P::sp(T(3)), P::fma(b, P::sp(T(-4)), a));
     const V t1 = P::add(P::fma(c, P::sp(T(-2)), b), d);
     const V u1 = P::fma(d, P::sp(T(-1)), b);
     const V t2 = P::add(P::fma(d, P::sp(T(-2)), c), e);
     const V u2 = P::fma(c, P::sp(T(3)), P::fma(d, P::sp(T(-4)), e));
+    const V q0 = P::fma(t0, P::sp(T(1.0 / 12.0)), P::mul(u0, P::sp(T(0.25))));   // q0 - c
+    const V q1 = P::fma(t1, P::sp(T(1.0 / 12.0)), P::mul(u1, P::sp(T(-0.25))));  // q1 - c
+    const V q2 = P::fma(t2, P::sp(T(1.0 / 12.0)), P::mul(u2, P::sp(T(-0.25))));  // q2 - c
     const V k13 = P::sp(T(13.0 / 12.0)), k14 = P::sp(T(0.25));
     V s0 = P::add(eps, P::fma(P::mul(t0, k13), t0, P::mul(P::mul(u0, u0), k14)));
     V s1 = P::add(eps, P::fma(P::mul(t1, k13), t1, P::mul(P::mul(u1, u1), k14)));
@@ -162,8 +169,10 @@ __device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typ
     s1 = P::mul(s1, s1);
     s2 = P::mul(s2, s2);
     const V p12 = P::mul(s1, s2), p02 = P::mul(s0, s2), p01 = P::mul(s0, s1);
-    const V num = P::fma(q2, p01, P::fma(q1, p02, P::mul(q0, p12)));
-    const V den = P::fma(p01, P::sp(T(0.3)), P::fma(p02, P::sp(T(0.6)), P::mul(p12, P::sp(T(0.1)))));
+    // linear weights d = (1/10, 6/10, 3/10) on the products
+    const V w0 = P::mul(p12, P::sp(T(0.1))), w1 = P::mul(p02, P::sp(T(0.6))), w2 = P::mul(p01, P::sp(T(0.3)));
+    const V num = P::fma(q2, w2, P::fma(q1, w1, P::mul(q0, w0)));
+    const V den = P::add(P::add(w0, w1), w2);
     return P::div(num, den);
 }
 
@@ -207,6 +216,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
     T* faces = tiles + (size_t)K * HXY;                  // [2][NF]
     double* red = reinterpret_cast<double*>(faces + 2 * NF);
+    __shared__ long long s_row[HY];                      // wrapped row offsets (edge tiles)
+    __shared__ int s_col[HXP];                           // wrapped columns (edge tiles)
 
     const int n_lat = g.hdr[0];
     const int total = g.hdr[1];
@@ -214,7 +225,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     const int tid = ty * TX + tx;
     const int in_idx = stage == 1 ? 0 : (stage == 2 ? 1 : 2);
     const int out_idx = stage == 1 ? 1 : (stage == 2 ? 2 : 0);
-    const T ca = stage == 1 ? T(0) : (stage == 2 ? T(0.75) : T(1.0 / 3.0));
+    // stage weights: f^(s) = f^n + cb ((u - f^n) + dt L(u)), i.e. the Shu-Osher
+    // combinations 3/4 f^n + 1/4 (u + dt L(u)) and 1/3 f^n + 2/3 (u + dt L(u))
     const T cb = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : T(2.0 / 3.0));
     // warp 0 also evaluates the faces on the tile's right and top edges:
     // lane l < TY: x-face right of node (TX-1, l); every lane: y-face above (l, TY-1)
@@ -250,23 +262,33 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         // 1. stage all K halo tiles of the stage input
         __syncthreads();  // the previous item is done with the tiles
         if (interior) {
-            // rows are 16-byte aligned: x0 - 4 is a multiple of 4, pitch of 32
+            // rows are 16-byte aligned (x0 - 4 is a multiple of 4, pitch of
+            // 32): every thread issues all its 16-byte asynchronous copies,
+            // then waits once
             constexpr int VEC = 16 / sizeof(T);
             constexpr int RV = HXP / VEC;
-            using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
             const T* src = U + (long long)(y0 - 3) * pitch + (x0 - 4);
+#pragma unroll 4
             for (int i = tid; i < K * HY * RV; i += NT) {
                 const int k = i / (HY * RV), rem = i - k * (HY * RV);
                 const int r = rem / RV, c = rem - r * RV;
-                const VT v = *reinterpret_cast<const VT*>(src + k * plane + (long long)r * pitch + c * VEC);
-                *reinterpret_cast<VT*>(tiles + (size_t)k * HXY + r * HXP + c * VEC) = v;
+                cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, src + k * plane + (long long)r * pitch + c * VEC);
             }
+            cp_async_wait_all();
         } else {
+            // periodic edge: wrapped row offsets and columns once per tile,
+            // then one asynchronous element copy per staged value
+            for (int i = tid; i < HY + HXP; i += NT) {
+                if (i < HY) s_row[i] = (long long)wrapi(y0 - 3 + i, ny) * pitch;
+                else s_col[i - HY] = wrapi(x0 - 4 + (i - HY), nx);
+            }
+            __syncthreads();
             for (int i = tid; i < K * HXY; i += NT) {
                 const int k = i / HXY, rem = i - k * HXY;
                 const int r = rem / HXP, c = rem - r * HXP;
-                tiles[i] = U[k * plane + (long long)wrapi(y0 - 3 + r, ny) * pitch + wrapi(x0 - 4 + c, nx)];
+                cp_async_small<sizeof(T)>(tiles + i, U + k * plane + s_row[r] + s_col[c]);
             }
+            cp_async_wait_all();
         }
         const T* __restrict__ fnp = Fn + cell;
         T* __restrict__ op = out + cell;
@@ -309,6 +331,25 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             block_reduce_obs<T, NT>(acc, dp->partials + (long long)local * NOBS, red);
         }
 
+        // FP32: residual moments of the collision term. In exact arithmetic
+        // sum_k (u_k - geq_k) (1, v_k) = 0; in float32 the rounding of the
+        // moments and of geq leaves a residual of ~1e-7 of the momentum per
+        // stage, which is not small next to the viscous decay per stage of a
+        // slowly decaying flow. It is computed from the differences u_k - geq_k
+        // (accurate) and removed below with w_k (R0 + v_k . R1), which has
+        // exactly these moments (quadrature identities of the set).
+        T R0 = T(0), R1x = T(0), R1y = T(0);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const T xi = (T)vx_of<Q1>(k) * ux + (T)vy_of<Q1>(k) * uy;
+                const T d = tiles[k * HXY + cidx] - (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                R0 += d;
+                if (vx_of<Q1>(k) != 0.0) R1x += d * (T)vx_of<Q1>(k);
+                if (vy_of<Q1>(k) != 0.0) R1y += d * (T)vy_of<Q1>(k);
+            }
+        }
+
         // 3. per population: the node's x- and y-face values (one pair),
         //    then the node update from the four faces around it
 #pragma unroll
@@ -342,15 +383,27 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             if (stage != 1 && active && k + 1 < K) fn_next = fnp[(k + 1) * plane];
             __syncthreads();
             if (active) {
+                // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-): the
+                // upwind node values c differ by one node (exact for close
+                // values), the corrections d are small
                 const T vx = (T)vxd, vy = (T)vyd;
-                T adv = T(0);
-                if (vxd != 0.0) adv -= (vx * cdx) * (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]);
-                if (vyd != 0.0) adv -= (vy * cdx) * (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]);
                 const T uk = tk[cidx];
+                T adv = T(0);
+                if (vxd != 0.0) {
+                    const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
+                    adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]));
+                }
+                if (vyd != 0.0) {
+                    const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
+                    adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]));
+                }
                 const T xi = vx * ux + vy * uy;
-                const T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
-                const T upd = uk + (adv - (uk - geq) * dtt);
-                op[k * plane] = stage == 1 ? upd : ca * fn + cb * upd;
+                T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                if constexpr (sizeof(T) == 4) geq += (T)w_of<Q1>(k) * (R0 + vx * R1x + vy * R1y);
+                const T inc = adv - (uk - geq) * dtt;  // dt L(u)_k
+                // stage combination in increment form: one rounding of the
+                // stored value per stage (u - f^n is exact for close values)
+                op[k * plane] = stage == 1 ? uk + inc : fn + cb * ((uk - fn) + inc);
             }
         }
     }

@@ -70,6 +70,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), cached
+// in L2 only; completes at cp_async_wait_all().
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// 4- or 8-byte asynchronous copy global -> shared (naturally aligned).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+    static_assert(BYTES == 4 || BYTES == 8, "4 or 8 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Barrier among the first `nthreads` threads after warp 0 of the block
 // (named barrier `id`, id != 0).
 __device__ __forceinline__ void named_sync(int id, int nthreads) {

@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (the same two-lattice batch, autotuned the same way): CS D2Q9 8192^2
+and FD 16-velocity 4096^2, FP32 deviation storage.
+
+The oracle cannot step these lattices whole, so it checks sampled windows:
+the state at step t is read in a W x W window (periodic, so windows at the
+lattice edges wrap) and the oracle advances that window, taken as a periodic
+lattice, by one step. A node's new value depends only on nodes within the
+update's reach (CS: 1; FD: 3 stages x 3 = 9), so the window's interior is the
+exact one-step result; the GPU's step t+1 is compared there.
+
+Tolerance: the GPU works in float32 on deviations g = f - w rho0; after one
+step its values carry O(10) roundings of numbers no larger than max|g| in the
+window, so agreement to 64 float32 ulps of that maximum is required.
+Global invariants are checked at full size as well: float64 mass conservation.
+"""
+import numpy as np
+import pytest
+
+import lbm_workloads as wl
+import oracle
+import paper_1904_02471_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+
+ULP32 = np.finfo(np.float32).eps
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1904_02471_gb300 import build
+    build.build()
+    torch.cuda.init()
+    cs, fd = wl.CS_ROOFLINE, wl.FD_ROOFLINE
+    specs = [pkg.make_spec("cs", 3, cs["nx"], cs["ny"], cs["tau"], 0.0, 0.0, "fp32"),
+             pkg.make_spec("fd", 4, fd["nx"], fd["ny"], fd["tau"], fd["dt"], 0.0, "fp32")]
+    B = pkg.Batch(specs)
+    for i, c in enumerate((cs, fd)):
+        B.init(i, *wl.taylor_green(c["nx"], c["ny"], c["U"]))
+        comp, px, py, norm = wl.probe_taylor_green(c["nx"], c["ny"])
+        B.set_probe(i, comp, px, py, norm)
+    B.tune(2)  # as bench.py
+    B.step(3)
+    B.sync()
+    yield B
+    B.close()
+
+
+def _windows(n, w, seed):
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0), (n - w // 2, n - w // 2), (n - 3, 5)]  # corners and edges wrap
+    pts += [tuple(int(v) for v in rng.integers(0, n, size=2)) for _ in range(4)]
+    return pts
+
+
+def _check(B, i, w, margin, advance, seed):
+    n = B.specs[i].nx
+    wins = _windows(n, w, seed)
+    before = [B.populations_region(i, x0, y0, w, w) for x0, y0 in wins]
+    B.step(1)
+    B.sync()
+    after = [B.populations_region(i, x0, y0, w, w) for x0, y0 in wins]
+    K = B.specs[i].q_per_axis ** 2
+    _, _, wk = pkg.lbm_velocity_set(B.specs[i].q_per_axis)
+    rho0 = B.specs[i].rho0 or 1.0
+    for (x0, y0), f0, f1 in zip(wins, before, after):
+        ref = advance(f0)
+        sl = (slice(None), slice(margin, w - margin), slice(margin, w - margin))
+        gmax = np.max(np.abs(f0 - wk.reshape(K, 1, 1) * rho0))
+        err = np.max(np.abs(f1[sl] - ref[sl]))
+        assert err <= 64 * ULP32 * gmax, ((x0, y0), err, gmax)
+
+
+def test_cs_8192_one_step_on_sampled_windows(batch):
+    cs = wl.CS_ROOFLINE
+    _check(batch, 0, 16, 1, lambda f: oracle.cs_run(f, cs["tau"], 1), seed=1)
+
+
+def test_fd_4096_one_step_on_sampled_windows(batch):
+    fd = wl.FD_ROOFLINE
+    _check(batch, 1, 24, 9, lambda f: oracle.fd_run(f, 1.0 / fd["nx"], fd["dt"], fd["tau"], 1), seed=2)
+
+
+def test_mass_is_conserved_at_full_size(batch):
+    o0 = [batch.observables(i) for i in range(2)]
+    batch.step(4)
+    o1 = [batch.observables(i) for i in range(2)]
+    for a, b in zip(o0, o1):
+        # float32 deviations of ~1e-3 rounded at ~1e-10 per node and step,
+        # summed in float64 over up to 6.7e7 nodes: far below 1e-9 relative
+        assert abs(b["mass"] - a["mass"]) <= 1e-9 * a["mass"]
+        assert b["nonfinite"] == 0
