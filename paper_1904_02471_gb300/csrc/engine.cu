@@ -378,6 +378,10 @@ int Engine::set_group_config(int gi, int tile, int grid) {
         set_error("no such tile variant");
         return LBM_EINVAL;
     }
+    if (g.model == LBM_FD && !fd_variant_fits(g.precision, g.q1, tile)) {
+        set_error("this FD tile variant needs more shared memory than the device offers for this set/precision");
+        return LBM_EINVAL;
+    }
     CK(cudaStreamSynchronize(stream_));
     g.tile = tile;
     g.grid = 0;

@@ -35,6 +35,9 @@ cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const Gro
 // Occupancy-based resident CTAs per SM of a variant (for persistent grids).
 int cs_blocks_per_sm(int precision, int tile);
 int fd_blocks_per_sm(int precision, int q1, int tile);
+// Whether an FD variant fits this device (shared memory); unfit variants are
+// refused by set_group_config and skipped by the autotuner.
+bool fd_variant_fits(int precision, int q1, int tile);
 
 // Fused-observables finalisation: lattices observing at sub-step j reduce
 // their tile partials (in nchunks chunks, scratch chunks[max_lat][nchunks][NOBS])

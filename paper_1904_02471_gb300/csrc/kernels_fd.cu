@@ -188,9 +188,15 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 constexpr int FD_TX = 32;
 constexpr int FD_HXP = 40;
 
-template <typename T, int TY>
-__host__ __device__ constexpr size_t fd_smem_bytes(int K) {
-    return sizeof(T) * ((size_t)K * (TY + 6) * FD_HXP + 2 * ((FD_TX + 1) * TY + FD_TX * (TY + 1))) +
+// Populations whose faces are evaluated between two barriers: 4, or 2 where
+// four face groups would not fit next to the halo tiles (FP64, 25 velocities).
+template <typename T, int Q1>
+__host__ __device__ constexpr int fd_group() { return (sizeof(T) == 8 && Q1 == 5) ? 2 : 4; }
+
+template <typename T, int Q1, int TY>
+__host__ __device__ constexpr size_t fd_smem_bytes() {
+    return sizeof(T) * ((size_t)Q1 * Q1 * (TY + 6) * FD_HXP +
+                        2 * fd_group<T, Q1>() * ((FD_TX + 1) * TY + FD_TX * (TY + 1))) +
            sizeof(double) * (FD_TX * TY / 32) * NOBS;
 }
 
@@ -213,9 +219,10 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     constexpr int NFY = TX * (TY + 1);   // faces normal to y: [TY + 1][TX]
     constexpr int NF = NFX + NFY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int G = fd_group<T, Q1>();
     T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
-    T* faces = tiles + (size_t)K * HXY;                  // [2][NF]
-    double* red = reinterpret_cast<double*>(faces + 2 * NF);
+    T* faces = tiles + (size_t)K * HXY;                  // [2][G][NF]
+    double* red = reinterpret_cast<double*>(faces + 2 * G * NF);
     __shared__ long long s_row[HY];                      // wrapped row offsets (edge tiles)
     __shared__ int s_col[HXP];                           // wrapped columns (edge tiles)
 
@@ -228,7 +235,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     // stage weights: f^(s) = f^n + cb ((u - f^n) + dt L(u)), i.e. the Shu-Osher
     // combinations 3/4 f^n + 1/4 (u + dt L(u)) and 1/3 f^n + 2/3 (u + dt L(u))
     const T cb = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : T(2.0 / 3.0));
-    // warp 0 also evaluates the faces on the tile's right and top edges:
+    // warp p of a group of G populations also evaluates the faces on the
+    // tile's right and top edges for the group's p-th population:
     // lane l < TY: x-face right of node (TX-1, l); every lane: y-face above (l, TY-1)
     const int ex_row = tx < TY ? tx : TY - 1;
     // per-thread bases in the staged tile (all stencil offsets are immediates)
@@ -292,7 +300,6 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         }
         const T* __restrict__ fnp = Fn + cell;
         T* __restrict__ op = out + cell;
-        T fn_next = (stage != 1 && active) ? fnp[0] : T(0);
         __syncthreads();
 
         // 2. moments of the stage input at this node, Eq. (f_moments_discrete)
@@ -350,60 +357,78 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             }
         }
 
-        // 3. per population: the node's x- and y-face values (one pair),
-        //    then the node update from the four faces around it
+        // 3. per group of G populations: every thread evaluates the x- and
+        //    y-face on the low side of its node for each population of the
+        //    group (one packed pair each), warps 0..G-1 add the edge faces,
+        //    one barrier, then every node updates those G populations from
+        //    the four faces around it. Face buffers alternate between groups.
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const T* tk = tiles + k * HXY;
-            T* fx = faces + (k & 1) * NF;   // [TY][TX + 1]
-            T* fy = fx + NFX;               // [TY + 1][TX]
-            const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
-            // upwind stencil of the face on the low side of node (c, r):
-            // x, v > 0: cols c+1..c+5 of row r+3; v < 0: cols c+6..c+2
-            // y, v > 0: rows r..r+4 of col c+4; v < 0: rows r+5..r+1
-            const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
-            const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
-            {
-                const T* px = tk + xrow + xo;
-                const T* py = tk + ycol + yo;
-                const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
-                                          P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
-                fx[ty * (TX + 1) + tx] = f.x;
-                fy[ty * TX + tx] = f.y;
+        for (int k0 = 0; k0 < K; k0 += G) {
+            T* fg = faces + ((k0 / G) & 1) * G * NF;
+            T fnv[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+                const int k = k0 + p;
+                if (k >= K) break;
+                const T* tk = tiles + k * HXY;
+                T* fx = fg + p * NF;            // [TY][TX + 1]
+                T* fy = fx + NFX;               // [TY + 1][TX]
+                const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
+                // upwind stencil of the face on the low side of node (c, r):
+                // x, v > 0: cols c+1..c+5 of row r+3; v < 0: cols c+6..c+2
+                // y, v > 0: rows r..r+4 of col c+4; v < 0: rows r+5..r+1
+                const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
+                const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
+                {
+                    const T* px = tk + xrow + xo;
+                    const T* py = tk + ycol + yo;
+                    const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                              P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                    fx[ty * (TX + 1) + tx] = f.x;
+                    fy[ty * TX + tx] = f.y;
+                }
+                if (ty == p % TY) {
+                    const T* px = tk + exrow + xo;
+                    const T* py = tk + eycol + yo;
+                    const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                              P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                    if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
+                    fy[TY * TX + tx] = f.y;
+                }
+                fnv[p] = (stage != 1 && active) ? fnp[k * plane] : T(0);
             }
-            if (ty == 0) {
-                const T* px = tk + exrow + xo;
-                const T* py = tk + eycol + yo;
-                const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
-                                          P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
-                if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
-                fy[TY * TX + tx] = f.y;
-            }
-            const T fn = fn_next;
-            if (stage != 1 && active && k + 1 < K) fn_next = fnp[(k + 1) * plane];
             __syncthreads();
             if (active) {
-                // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-): the
-                // upwind node values c differ by one node (exact for close
-                // values), the corrections d are small
-                const T vx = (T)vxd, vy = (T)vyd;
-                const T uk = tk[cidx];
-                T adv = T(0);
-                if (vxd != 0.0) {
-                    const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
-                    adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]));
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    const int k = k0 + p;
+                    if (k >= K) break;
+                    const T* tk = tiles + k * HXY;
+                    const T* fx = fg + p * NF;
+                    const T* fy = fx + NFX;
+                    const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
+                    // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-): the
+                    // upwind node values c differ by one node (exact for close
+                    // values), the corrections d are small
+                    const T vx = (T)vxd, vy = (T)vyd;
+                    const T uk = tk[cidx];
+                    T adv = T(0);
+                    if (vxd != 0.0) {
+                        const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
+                        adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]));
+                    }
+                    if (vyd != 0.0) {
+                        const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
+                        adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]));
+                    }
+                    const T xi = vx * ux + vy * uy;
+                    T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                    if constexpr (sizeof(T) == 4) geq += (T)w_of<Q1>(k) * (R0 + vx * R1x + vy * R1y);
+                    const T inc = adv - (uk - geq) * dtt;  // dt L(u)_k
+                    // stage combination in increment form: one rounding of the
+                    // stored value per stage (u - f^n is exact for close values)
+                    op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
                 }
-                if (vyd != 0.0) {
-                    const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
-                    adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]));
-                }
-                const T xi = vx * ux + vy * uy;
-                T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
-                if constexpr (sizeof(T) == 4) geq += (T)w_of<Q1>(k) * (R0 + vx * R1x + vy * R1y);
-                const T inc = adv - (uk - geq) * dtt;  // dt L(u)_k
-                // stage combination in increment form: one rounding of the
-                // stored value per stage (u - f^n is exact for close values)
-                op[k * plane] = stage == 1 ? uk + inc : fn + cb * ((uk - fn) + inc);
             }
         }
     }
@@ -441,13 +466,23 @@ static const void* fd_kernel_ptr(int tile, int q1) {
     return nullptr;
 }
 
-template <typename T>
-static size_t fd_smem(int tile, int K) {
+template <typename T, int Q1>
+static size_t fd_smem_q(int tile) {
     switch (tile) {
-        case FD_T32x8: return fd_smem_bytes<T, 8>(K);
-        case FD_T32x4: return fd_smem_bytes<T, 4>(K);
-        case FD_T32x16: return fd_smem_bytes<T, 16>(K);
-        case FD_T32x2: return fd_smem_bytes<T, 2>(K);
+        case FD_T32x8: return fd_smem_bytes<T, Q1, 8>();
+        case FD_T32x4: return fd_smem_bytes<T, Q1, 4>();
+        case FD_T32x16: return fd_smem_bytes<T, Q1, 16>();
+        case FD_T32x2: return fd_smem_bytes<T, Q1, 2>();
+    }
+    return 0;
+}
+
+template <typename T>
+static size_t fd_smem(int tile, int q1) {
+    switch (q1) {
+        case 3: return fd_smem_q<T, 3>(tile);
+        case 4: return fd_smem_q<T, 4>(tile);
+        case 5: return fd_smem_q<T, 5>(tile);
     }
     return 0;
 }
@@ -456,19 +491,38 @@ static const void* fd_fn(int precision, int tile, int q1) {
     return precision == LBM_FP64 ? fd_kernel_ptr<double>(tile, q1) : fd_kernel_ptr<float>(tile, q1);
 }
 static size_t fd_bytes(int precision, int tile, int q1) {
-    return precision == LBM_FP64 ? fd_smem<double>(tile, q1 * q1) : fd_smem<float>(tile, q1 * q1);
+    return precision == LBM_FP64 ? fd_smem<double>(tile, q1) : fd_smem<float>(tile, q1);
 }
 
 // Opt each variant into the dynamic shared memory it needs; once per process.
+// A variant that cannot fit on this device is refused (and the CUDA error
+// state cleared).
 static cudaError_t fd_prepare(int precision, int tile, int q1) {
-    static bool done[2][FD_NTILES][3] = {};
+    static int state[2][FD_NTILES][3] = {};  // 0 unknown, 1 ready, 2 does not fit
     const int p = precision == LBM_FP64 ? 0 : 1;
-    if (done[p][tile][q1 - 3]) return cudaSuccess;
+    int& st = state[p][tile][q1 - 3];
+    if (st == 1) return cudaSuccess;
+    if (st == 2) return cudaErrorInvalidConfiguration;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaErrorInvalidConfiguration;
+    }
     const size_t need = fd_bytes(precision, tile, q1);
+    if (need > (size_t)optin) {
+        st = 2;
+        return cudaErrorInvalidConfiguration;
+    }
     cudaError_t e = cudaFuncSetAttribute(fd_fn(precision, tile, q1), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)need);
-    if (e == cudaSuccess) done[p][tile][q1 - 3] = true;
-    return e;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st = 2;
+        return cudaErrorInvalidConfiguration;
+    }
+    st = 1;
+    return cudaSuccess;
 }
 
 cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const GroupDev& g, int j, int stage,
@@ -484,8 +538,12 @@ cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const Gro
     return cudaLaunchKernel(fn, dim3(grid), dim3(fd_tile_tx(tile), fd_tile_ty(tile)), args, fd_bytes(precision, tile, q1), s);
 }
 
+bool fd_variant_fits(int precision, int q1, int tile) {
+    return tile >= 0 && tile < FD_NTILES && q1 >= 3 && q1 <= 5 && fd_prepare(precision, tile, q1) == cudaSuccess;
+}
+
 int fd_blocks_per_sm(int precision, int q1, int tile) {
-    if (tile < 0 || tile >= FD_NTILES || q1 < 3 || q1 > 5 || fd_prepare(precision, tile, q1) != cudaSuccess) return 1;
+    if (!fd_variant_fits(precision, q1, tile)) return 1;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile, q1), fd_tile_tx(tile) * fd_tile_ty(tile),
                                                       fd_bytes(precision, tile, q1)) != cudaSuccess)

@@ -347,7 +347,11 @@ def test_fd_every_tile_variant(prec, q, nx, ny):
     for tile in range(lbm.lbm_n_tiles("fd")):
         for grid in (0, 3):
             with pkg.Lattice("fd", q, nx, ny, tau, dt=dt, precision=prec) as L:
-                L.config(tile, grid)
+                try:
+                    L.config(tile, grid)
+                except lbm.LbmError as e:  # variant too large for this set and precision
+                    assert e.code == lbm.LBM_EINVAL and "shared memory" in str(e)
+                    continue
                 L.set_populations(f0)
                 L.step(12)
                 res.append(((tile, grid), L.populations()))
