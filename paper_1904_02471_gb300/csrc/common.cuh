@@ -49,7 +49,18 @@ struct LatDesc {
     double* partials;       // [items][NOBS], this lattice's slice
     lbm_obs* series;        // [obs_cap]
     double* snap;           // [NOBS] result of a one-off observables reduction
+    // float copies of omega, cdx, dt_tau, rho0, eps for the FP32 kernels (a
+    // conversion from double would run on the narrow FP64 pipe every tile)
+    float omega_f, cdx_f, dt_tau_f, rho0_f, eps_f;
 };
+
+// A per-lattice constant in the kernel's precision.
+template <typename T>
+__device__ __forceinline__ T lat_val(double d, float f);
+template <>
+__device__ __forceinline__ double lat_val<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float lat_val<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------------------
 // Gauss-Hermite nodes and weights (probabilists', weights summing to 1):

@@ -276,6 +276,11 @@ LatDesc Engine::make_desc(const Lattice& L, const Group& g, int item_begin, doub
     d.dt_tau = L.dt_tau;
     d.rho0 = L.rho0s;
     d.eps = L.eps;
+    d.omega_f = (float)L.omega;
+    d.cdx_f = (float)L.cdx;
+    d.dt_tau_f = (float)L.dt_tau;
+    d.rho0_f = (float)L.rho0s;
+    d.eps_f = (float)L.eps;
     d.dt = L.spec.dt;
     d.probe_comp = L.probe_comp;
     d.obs_cap = (int)std::min<long long>(L.obs_cap, std::numeric_limits<int>::max());

@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
         const int cur = dp->cur ^ (j & 1);
         const T* __restrict__ in = static_cast<const T*>(dp->buf[cur]);
         T* __restrict__ out = static_cast<T*>(dp->buf[cur ^ 1]);
-        const T omega = (T)dp->omega;
-        const T r0 = (T)dp->rho0;
+        const T omega = lat_val<T>(dp->omega, dp->omega_f);
+        const T r0 = lat_val<T>(dp->rho0, dp->rho0_f);
         const bool obs = observe_now(*dp, j);
         const int pc = dp->probe_comp;
         T acc[NOBS] = {T(0), T(0), T(0), T(0)};
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
         const int cur = dp->cur ^ (j & 1);
         const T* __restrict__ in = static_cast<const T*>(dp->buf[cur]);
         T* __restrict__ out = static_cast<T*>(dp->buf[cur ^ 1]);
-        const T omega = (T)dp->omega;
-        const T r0 = (T)dp->rho0;
+        const T omega = lat_val<T>(dp->omega, dp->omega_f);
+        const T r0 = lat_val<T>(dp->rho0, dp->rho0_f);
         const bool obs = observe_now(*dp, j);
         const int pc = dp->probe_comp;
         const int x = x0 + ctid;

@@ -117,7 +117,14 @@ struct Pr<float> {
     static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
     static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
-    static __device__ __forceinline__ V div(V a, V b) { return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y)); }
+    // a / b through the approximate reciprocal (relative error ~2^-23):
+    // b is a normal number far from the range limits here
+    static __device__ __forceinline__ float rcp(float x) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ V div(V a, V b) { return __fmul2_rn(a, make_float2(rcp(b.x), rcp(b.y))); }
 };
 
 template <>
@@ -131,46 +138,47 @@ struct Pr<double> {
     static __device__ __forceinline__ V div(V a, V b) { return make_double2(a.x / b.x, a.y / b.y); }
 };
 
-// WENO-5 interface values (Jiang-Shu) of two faces at once, as corrections
-// face - c to the upwind node value c (see below), from their
+// WENO-5 interface values (Jiang-Shu) of two faces at once, from their
 // upwind-ordered stencils (a, b, c, d, e) = (f_{i-2}, f_{i-1}, f_i, f_{i+1},
 // f_{i+2}) for the face i+1/2:
 //   candidates q0 = (2a - 7b + 11c)/6, q1 = (-b + 5c + 2d)/6, q2 = (2c + 5d - e)/6,
-//   smoothness beta_r = 13/12 (second difference)^2 + 1/4 (first difference)^2,
+//   smoothness beta_r = 13/12 t_r^2 + 1/4 u_r^2 with the second differences
+//     t_r and the first differences u0 = a - 4b + 3c, u1 = b - d,
+//     u2 = 3c - 4d + e of the three stencils,
 //   weights alpha_r = d_r / (eps + beta_r)^2, d = (1/10, 6/10, 3/10),
 //   face = sum alpha_r q_r / sum alpha_r.
-// Numerator and denominator are multiplied by s0 s1 s2 (s_r = (eps +
-// beta_r)^2), so a face costs one division.
+// The normalised weights do not change when every alpha_r is multiplied by
+// one common factor, so the kernel uses s_r = (12/13)(eps + beta_r) =
+// t_r^2 + (3/13) u_r^2 + e (e = 12 eps / 13, passed in), d = (1, 6, 3), and
+// multiplies numerator and denominator by s0^2 s1^2 s2^2: one reciprocal per
+// face. All differences come from the four node differences D_i = f_{i+1} - f_i
+// of the stencil (exact for close values). With q_r = c + (t_r + 3 u_r')/12
+// (u_r' = u0, -u1, -u2) the function returns 12 (face - c): a small number
+// next to c, so its rounding is small next to the flux differences it feeds.
 template <typename T>
 __device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typename Pr<T>::V b, typename Pr<T>::V c,
-                                                        typename Pr<T>::V d, typename Pr<T>::V e, typename Pr<T>::V eps) {
+                                                        typename Pr<T>::V d, typename Pr<T>::V e, typename Pr<T>::V eps_s) {
     using P = Pr<T>;
     using V = typename P::V;
-    // second differences t_r and one-sided / central first differences u_r of
-    // the three stencils; the candidates follow from them:
-    // q0 = c + t0/12 + u0/4, q1 = c + t1/12 - u1/4, q2 = c + t2/12 - u2/4.
-    // The function returns face - c, the correction to the upwind node value
-    // c: a small number, so its rounding error is small next to the flux
-    // differences it feeds (see the node update).
-    const V t0 = P::add(P::fma(b, P::sp(T(-2)), a), c);
-    const V u0 = P::fma(c, P::sp(T(3)), P::fma(b, P::sp(T(-4)), a));
-    const V t1 = P::add(P::fma(c, P::sp(T(-2)), b), d);
-    const V u1 = P::fma(d, P::sp(T(-1)), b);
-    const V t2 = P::add(P::fma(d, P::sp(T(-2)), c), e);
-    const V u2 = P::fma(c, P::sp(T(3)), P::fma(d, P::sp(T(-4)), e));
-    const V q0 = P::fma(t0, P::sp(T(1.0 / 12.0)), P::mul(u0, P::sp(T(0.25))));   // q0 - c
-    const V q1 = P::fma(t1, P::sp(T(1.0 / 12.0)), P::mul(u1, P::sp(T(-0.25))));  // q1 - c
-    const V q2 = P::fma(t2, P::sp(T(1.0 / 12.0)), P::mul(u2, P::sp(T(-0.25))));  // q2 - c
-    const V k13 = P::sp(T(13.0 / 12.0)), k14 = P::sp(T(0.25));
-    V s0 = P::add(eps, P::fma(P::mul(t0, k13), t0, P::mul(P::mul(u0, u0), k14)));
-    V s1 = P::add(eps, P::fma(P::mul(t1, k13), t1, P::mul(P::mul(u1, u1), k14)));
-    V s2 = P::add(eps, P::fma(P::mul(t2, k13), t2, P::mul(P::mul(u2, u2), k14)));
+    const V m1 = P::sp(T(-1));
+    const V D1 = P::fma(a, m1, b), D2 = P::fma(b, m1, c), D3 = P::fma(c, m1, d), D4 = P::fma(d, m1, e);
+    const V t0 = P::fma(D1, m1, D2), t1 = P::fma(D2, m1, D3), t2 = P::fma(D3, m1, D4);
+    const V u0 = P::fma(D2, P::sp(T(-3)), D1);   // -(a - 4b + 3c)
+    const V u1 = P::add(D2, D3);                  // d - b
+    const V u2 = P::fma(D3, P::sp(T(-3)), D4);   // 3c - 4d + e
+    const V q0 = P::fma(u0, P::sp(T(-3)), t0);   // 12 (q0 - c)
+    const V q1 = P::fma(u1, P::sp(T(3)), t1);    // 12 (q1 - c)
+    const V q2 = P::fma(u2, P::sp(T(-3)), t2);   // 12 (q2 - c)
+    const V k = P::sp(T(3.0 / 13.0));
+    V s0 = P::fma(t0, t0, P::fma(P::mul(u0, k), u0, eps_s));
+    V s1 = P::fma(t1, t1, P::fma(P::mul(u1, k), u1, eps_s));
+    V s2 = P::fma(t2, t2, P::fma(P::mul(u2, k), u2, eps_s));
     s0 = P::mul(s0, s0);
     s1 = P::mul(s1, s1);
     s2 = P::mul(s2, s2);
-    const V p12 = P::mul(s1, s2), p02 = P::mul(s0, s2), p01 = P::mul(s0, s1);
-    // linear weights d = (1/10, 6/10, 3/10) on the products
-    const V w0 = P::mul(p12, P::sp(T(0.1))), w1 = P::mul(p02, P::sp(T(0.6))), w2 = P::mul(p01, P::sp(T(0.3)));
+    const V w0 = P::mul(s1, s2);                          // d0 s1^2 s2^2
+    const V w1 = P::mul(P::mul(s0, s2), P::sp(T(6)));     // d1 s0^2 s2^2
+    const V w2 = P::mul(P::mul(s0, s1), P::sp(T(3)));     // d2 s0^2 s1^2
     const V num = P::fma(q2, w2, P::fma(q1, w1, P::mul(q0, w0)));
     const V den = P::add(P::add(w0, w1), w2);
     return P::div(num, den);
@@ -260,10 +268,10 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         const T* __restrict__ U = static_cast<const T*>(dp->buf[in_idx]);
         const T* __restrict__ Fn = static_cast<const T*>(dp->buf[0]);
         T* __restrict__ out = static_cast<T*>(dp->buf[out_idx]);
-        const T r0 = (T)dp->rho0;
-        const T cdx = (T)dp->cdx;
-        const T dtt = (T)dp->dt_tau;
-        const V eps = P::sp((T)dp->eps);
+        const T r0 = lat_val<T>(dp->rho0, dp->rho0_f);
+        const T cdx = lat_val<T>(dp->cdx, dp->cdx_f);
+        const T dtt = lat_val<T>(dp->dt_tau, dp->dt_tau_f);
+        const V eps = P::sp(lat_val<T>(dp->eps, dp->eps_f) * T(12.0 / 13.0));
         const long long cell = (long long)y * pitch + x;
         const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
 
@@ -407,19 +415,19 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     const T* fx = fg + p * NF;
                     const T* fy = fx + NFX;
                     const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
-                    // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-): the
-                    // upwind node values c differ by one node (exact for close
-                    // values), the corrections d are small
+                    // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-)/12:
+                    // the upwind node values c differ by one node (exact for
+                    // close values), the stored corrections d = 12 (face - c) are small
                     const T vx = (T)vxd, vy = (T)vyd;
                     const T uk = tk[cidx];
                     T adv = T(0);
                     if (vxd != 0.0) {
                         const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
-                        adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]));
+                        adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * T(1.0 / 12.0));
                     }
                     if (vyd != 0.0) {
                         const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
-                        adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]));
+                        adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * T(1.0 / 12.0));
                     }
                     const T xi = vx * ux + vy * uy;
                     T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
