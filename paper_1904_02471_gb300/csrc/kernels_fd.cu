@@ -353,17 +353,25 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         // slowly decaying flow. It is computed from the differences u_k - geq_k
         // (accurate) and removed below with w_k (R0 + v_k . R1), which has
         // exactly these moments (quadrature identities of the set).
+        // The stored equilibrium is written w_k (dr + v_k . j + rho/2 ((v_k . u)^2
+        // - u^2)), i.e. Eq. (herfeq) minus w_k rho0 with rho (v_k . u) = v_k . j.
+        const T hr = T(0.5) * rho;
         T R0 = T(0), R1x = T(0), R1y = T(0);
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const T xi = (T)vx_of<Q1>(k) * ux + (T)vy_of<Q1>(k) * uy;
-                const T d = tiles[k * HXY + cidx] - (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                const T vx = (T)vx_of<Q1>(k), vy = (T)vy_of<Q1>(k);
+                const T xi = vx * ux + vy * uy;
+                const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jx + (vy * jy + dr)));
+                const T d = tiles[k * HXY + cidx] - geq;
                 R0 += d;
-                if (vx_of<Q1>(k) != 0.0) R1x += d * (T)vx_of<Q1>(k);
-                if (vy_of<Q1>(k) != 0.0) R1y += d * (T)vy_of<Q1>(k);
+                if (vx_of<Q1>(k) != 0.0) R1x += d * vx;
+                if (vy_of<Q1>(k) != 0.0) R1y += d * vy;
             }
         }
+        // the correction w_k (R0 + v_k . R1) enters the equilibrium as
+        // shifted moments: dr + R0, j + R1
+        const T drc = dr + R0, jxc = jx + R1x, jyc = jy + R1y;
 
         // 3. per group of G populations: every thread evaluates the x- and
         //    y-face on the low side of its node for each population of the
@@ -420,19 +428,20 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     // close values), the stored corrections d = 12 (face - c) are small
                     const T vx = (T)vxd, vy = (T)vyd;
                     const T uk = tk[cidx];
-                    T adv = T(0);
+                    // a = v_x dF_x + v_y dF_y (zero components drop out)
+                    T a = T(0);
                     if (vxd != 0.0) {
                         const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
-                        adv -= (vx * cdx) * (dc + (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * T(1.0 / 12.0));
+                        a = vx * ((fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * T(1.0 / 12.0) + dc);
                     }
                     if (vyd != 0.0) {
                         const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
-                        adv -= (vy * cdx) * (dc + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * T(1.0 / 12.0));
+                        a += vy * ((fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * T(1.0 / 12.0) + dc);
                     }
                     const T xi = vx * ux + vy * uy;
-                    T geq = (T)w_of<Q1>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
-                    if constexpr (sizeof(T) == 4) geq += (T)w_of<Q1>(k) * (R0 + vx * R1x + vy * R1y);
-                    const T inc = adv - (uk - geq) * dtt;  // dt L(u)_k
+                    const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jxc + (vy * jyc + drc)));
+                    // dt L(u)_k = -(dt/dx) a - (u - geq) dt/tau
+                    const T inc = (geq - uk) * dtt - a * cdx;
                     // stage combination in increment form: one rounding of the
                     // stored value per stage (u - f^n is exact for close values)
                     op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
