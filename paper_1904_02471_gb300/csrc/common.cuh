@@ -147,8 +147,9 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 // Block reduction of NOBS per-thread partial sums into out[NOBS] (double).
 // Warp level in T (for FP32 storage: at most 32 per-thread sums in float),
 // across warps in double, fixed order (deterministic).
-// Must be called by all threads of the block.
-template <typename T, int NT>
+// Must be called by all threads of the block. With TRAILING_SYNC false the
+// caller guarantees a barrier before `smem` is written again.
+template <typename T, int NT, bool TRAILING_SYNC = true>
 __device__ __forceinline__ void block_reduce_obs(const T (&v)[NOBS], double* out, double* smem) {
     constexpr int NW = NT / 32;
     T r[NOBS];
@@ -172,7 +173,7 @@ __device__ __forceinline__ void block_reduce_obs(const T (&v)[NOBS], double* out
         for (int w = 0; w < NW; ++w) s += smem[w * NOBS + tid];
         out[tid] = s;
     }
-    __syncthreads();
+    if constexpr (TRAILING_SYNC) __syncthreads();
 }
 
 }  // namespace lbm

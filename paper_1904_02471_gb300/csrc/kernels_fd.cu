@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     double* red = reinterpret_cast<double*>(faces + 2 * G * NF);
     __shared__ long long s_row[HY];                      // wrapped row offsets (edge tiles)
     __shared__ int s_col[HXP];                           // wrapped columns (edge tiles)
+    __shared__ int s_obs;                                // record observables for this item
 
     const int n_lat = g.hdr[0];
     const int total = g.hdr[1];
@@ -276,7 +277,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
 
         // 1. stage all K halo tiles of the stage input
-        __syncthreads();  // the previous item is done with the tiles
+        __syncthreads();  // the previous item is done with the tiles (and s_obs)
+        if (tid == 0) s_obs = stage == 1 && observe_now(*dp, j);
         if (interior) {
             // rows are 16-byte aligned (x0 - 4 is a multiple of 4, pitch of
             // 32): every thread issues all its 16-byte asynchronous copies,
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         const T ux = jx * inv, uy = jy * inv;
         const T usq = ux * ux + uy * uy;
 
-        if (stage == 1 && observe_now(*dp, j)) {
+        if (s_obs) {
             T acc[NOBS] = {T(0), T(0), T(0), T(0)};
             if (active) {
                 acc[0] = dr;
@@ -343,7 +345,9 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     acc[3] = (pc == 0 ? ux : uy) * pxv * pyv;
                 }
             }
-            block_reduce_obs<T, NT>(acc, dp->partials + (long long)local * NOBS, red);
+            // no trailing barrier: `red` is next written after the next
+            // item's staging barrier
+            block_reduce_obs<T, NT, false>(acc, dp->partials + (long long)local * NOBS, red);
         }
 
         // FP32: residual moments of the collision term. In exact arithmetic
