@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import math
 import os
 import statistics
@@ -49,6 +50,17 @@ WORKLOAD = "roofline lattices: CS D2Q9 8192^2 + FD 16-velocity 4096^2, FP32 devi
 # an FD step reads Q, 2Q, 2Q and writes Q, Q, Q values over its three stages.
 CS_BYTES_LU = 18 * 4
 FD_BYTES_LU = 8 * 16 * 4
+# Algorithmic FP32 flops of one FD lattice update (3 RK stages, 16
+# populations), counted from the textbook formulas, every +, -, x, / one flop:
+# per population and stage two WENO-5 interfaces (one per axis; an interface
+# is shared by the two nodes it separates) of 64 flops each (candidates 15,
+# smoothness indicators 30, weights 19) plus 3 for the flux difference, 13 for
+# the equilibrium, BGK and stage combination, 3 for the moments.
+WENO5_FLOPS = 64
+FD_FLOPS_LU = 3 * 16 * (2 * (WENO5_FLOPS + 3) + 13 + 3)
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops
+# (an FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def peaks():
@@ -238,6 +250,8 @@ def run_gpu(args, rank, world):
     cs_gbs = CS_N * CS_N * CS_BYTES_LU / (cs_ms / 1e3) / 1e9
     fd_stage_avg = sum(fd_stage_ms) / 3
     fd_gbs = FD_N * FD_N * FD_BYTES_LU / 3 / (fd_stage_avg / 1e3) / 1e9
+    fd_tflops = FD_N * FD_N * FD_FLOPS_LU / 3 / (fd_stage_avg / 1e3) / 1e12
+    fd_ty = fd_tile_height(tune_report, gfd)
     traffic = committed_traffic()
     rec = {
         "metric": METRIC,
@@ -270,11 +284,15 @@ def run_gpu(args, rank, world):
                    "gbs": round(fd_gbs, 1), "frac_hbm": round(fd_gbs / peak, 3), "bytes_per_lu": FD_BYTES_LU},
             "finalize_ms_per_step": round(fin_ms, 4),
         },
-        "roofline": {"kernel": "fd_stage_kernel<float,32,*> (FD RK stage, Q=16)", "bound": "hbm",
-                     "achieved": round(fd_gbs, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(fd_gbs / peak, 4), "peak_source": peak_kind,
+        "roofline": {"kernel": f"fd_stage_kernel<float,4,{fd_ty}> (FD RK stage, Q=16)", "bound": "alu",
+                     "achieved": round(fd_tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                     "frac": round(fd_tflops / FP32_PEAK_TFLOPS, 4),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                      "traffic": traffic.get("fd_stage") if traffic else None,
-                     "algorithmic_bytes_per_launch": FD_N * FD_N * FD_BYTES_LU // 3},
+                     "algorithmic_flops_per_launch": FD_N * FD_N * FD_FLOPS_LU // 3,
+                     "algorithmic_bytes_per_launch": FD_N * FD_N * FD_BYTES_LU // 3,
+                     "hbm": {"achieved": round(fd_gbs, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(fd_gbs / peak, 4), "peak_source": peak_kind}},
         "e2e": {"value": round(world * cells * K / e_wall / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -425,6 +443,16 @@ def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=
                       "max": round(lat[-1], 4)},
         "makespan_s": round(makespan, 3),
     }
+
+
+def fd_tile_height(report, gi):
+    """Tile height of the FD group's kernel variant, from the tuner's report."""
+    m = re.search(rf"\[g{gi} FD q4 fp32 (cached )?tile=(\d+)(x(\d+))?", report)
+    if not m:
+        return "*"
+    if m.group(4):
+        return m.group(4)
+    return {0: "8", 1: "4", 2: "16", 3: "2"}.get(int(m.group(2)), "*")
 
 
 def committed_traffic():
