@@ -456,8 +456,8 @@ def fd_tile_height(report, gi):
 
 
 def committed_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu summary, per kernel, for
+    the kernels whose sources have not changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -465,9 +465,8 @@ def committed_traffic():
         from paper_1904_02471_gb300 import build
         with open(p) as fh:
             d = json.load(fh)
-        if d.get("source_digest") != build.kernel_digest():
-            return None
-        return d.get("bytes_per_launch")
+        return {k: v["bytes_per_launch"] for k, v in d.get("kernels", {}).items()
+                if v.get("source_digest") == build.kernel_digest(k)}
     except Exception:
         return None
 

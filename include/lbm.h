@@ -373,6 +373,22 @@ int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* 
 /* Cancel what is left, stop the worker and free everything. */
 void lbm_server_destroy(lbm_server* s);
 
+/* Test injection of a device-side wait that runs out (no counterpart in the
+ * paper; failure detection of the library itself). The CS bulk-copy kernel
+ * (the default CS kernel; the only one with device-side waits) bounds every
+ * mbarrier wait by 2 s of device time; with microseconds > 0, every wait of
+ * the following CS launches is bounded by that many microseconds and the
+ * first block skips the copies of its first row, so that row's consumers wait
+ * on a barrier that nothing completes. The wait runs out, the launch sets the
+ * group's error word and finishes (no fault, no unbounded wait, copies in
+ * flight land first), and lbm_sync / lbm_batch_sync return LBM_ETIMEOUT; the
+ * state of that step is invalid. 0 turns the injection off. Range 0..1e6,
+ * else LBM_EINVAL. The server variant applies from the next round and fails
+ * the runs of that round with LBM_ETIMEOUT (reported by lbm_poll). */
+int lbm_inject_wait_timeout(lbm_ctx* ctx, int microseconds);
+int lbm_batch_inject_wait_timeout(lbm_batch* b, int microseconds);
+int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds);
+
 /* ---- observables without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory: code issued while a stream is being

@@ -46,12 +46,20 @@ def _digest(extra=()) -> str:
     return h.hexdigest()
 
 
-def kernel_digest() -> str:
-    """Digest of the kernel sources alone (identifies the build a profile was taken on)."""
+KERNEL_SOURCES = {
+    "fd_stage": ["kernels_fd.cu"],
+    "cs_bulk": ["kernels_cs.cu"],
+}
+SHARED_SOURCES = ["common.cuh", "ptx.cuh", "kernels.h"]
+
+
+def kernel_digest(kernel: str) -> str:
+    """Digest of one kernel's sources and the headers it includes (identifies
+    the build a profile of that kernel was taken on)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(CSRC, "kernels*")) + [os.path.join(CSRC, "common.cuh")]):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
+    for f in KERNEL_SOURCES[kernel] + SHARED_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -193,6 +193,20 @@ int lbm_step(lbm_ctx* c, int64_t n) {
     GUARD_END
 }
 
+int lbm_inject_wait_timeout(lbm_ctx* c, int microseconds) {
+    GUARD_BEGIN
+    if (!c) return LBM_EINVAL;
+    return c->e.inject_wait_timeout(microseconds);
+    GUARD_END
+}
+
+int lbm_batch_inject_wait_timeout(lbm_batch* b, int microseconds) {
+    GUARD_BEGIN
+    if (!b) return LBM_EINVAL;
+    return b->e.inject_wait_timeout(microseconds);
+    GUARD_END
+}
+
 int lbm_sync(lbm_ctx* c) {
     GUARD_BEGIN
     if (!c) return LBM_EINVAL;

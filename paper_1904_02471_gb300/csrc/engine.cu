@@ -356,7 +356,7 @@ int Engine::upload_group(int gi) {
         lat[g.members[m]].slot = m;
         descs.push_back(make_desc(lat[g.members[m]], g, begins[m], g.d_partials + (long long)begins[m] * NOBS));
     }
-    const int hdr[4] = {nm, (int)items, 0, 0};
+    const int hdr[4] = {nm, (int)items, 0, inject_us_};
     if (nm) {
         CK(cudaMemcpyAsync(g.d_desc, descs.data(), sizeof(LatDesc) * nm, cudaMemcpyHostToDevice, stream_));
         CK(cudaMemcpyAsync(g.d_item_begin, begins.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, stream_));
@@ -560,6 +560,20 @@ int Engine::sync() {
     CK(cudaStreamSynchronize(stream_));
     CK(cudaGetLastError());
     return check_device_errors();
+}
+
+int Engine::inject_wait_timeout(int us) {
+    if (us < 0 || us > 1000000) {
+        set_error("wait-timeout injection takes 0 (off) to 1e6 microseconds");
+        return LBM_EINVAL;
+    }
+    inject_us_ = us;
+    for (auto& g : groups) {
+        if (!g.d_hdr) continue;
+        CK(cudaMemcpyAsync(g.d_hdr + 3, &inject_us_, sizeof(int), cudaMemcpyHostToDevice, stream_));
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return LBM_OK;
 }
 
 // Error words the kernels raise instead of hanging (bounded waits that ran

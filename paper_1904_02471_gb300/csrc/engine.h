@@ -95,6 +95,7 @@ class Engine {
     int remove_lattice(int i);
     static size_t footprint(const lbm_spec& s);  // device bytes of one lattice
     bool dynamic_ = false;   // persistent grids sized for the machine, not the current work
+    int inject_us_ = 0;      // group header word 3 (wait-timeout injection)
     static int validate(const lbm_spec* in, lbm_spec* out);
 
     int n_lattices() const { return (int)lat.size(); }
@@ -113,6 +114,9 @@ class Engine {
     long long kernel_launches() const { return launches_; }
     int sync();
     int check_device_errors();
+    // Test injection of a device-side wait that runs out (see lbm.h,
+    // lbm_inject_wait_timeout): 0 = off, else the wait limit in microseconds.
+    int inject_wait_timeout(int microseconds);
     int moments(int i, double* rho, double* ux, double* uy);
     int populations(int i, double* f);
     int populations_region(int i, int x0, int y0, int wx, int wy, double* f);

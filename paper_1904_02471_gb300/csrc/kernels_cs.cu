@@ -112,7 +112,10 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
 // and every buffer has a tail pad), and it contains the x-1 / x+1 neighbours;
 // only the periodic wrap at x = 0 / nx - 1 is read from global memory.
 // All waits are bounded; a timeout sets hdr[2] and the block finishes
-// without waiting again.
+// without waiting again. hdr[3] > 0 is a test injection: every wait of the
+// launch is limited to hdr[3] microseconds and block 0's producer skips the
+// copies of its first row, so that row's consumers wait on a barrier nothing
+// completes and run out of time (no fault, no unbounded wait).
 template <typename T, int W, int RB, int S>
 __host__ __device__ constexpr size_t cs_bulk_smem() {
     return (size_t)S * 9 * (W + 8) * sizeof(T) + 2 * S * sizeof(uint64_t) + (W / 32) * NOBS * sizeof(double);
@@ -141,12 +144,15 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
     __syncthreads();
     const int n_lat = g.hdr[0];
     const int total = g.hdr[1];
+    const int inject_us = g.hdr[3];
+    const unsigned long long lim = inject_us > 0 ? 1000ull * (unsigned long long)inject_us : WAIT_NS;
 
     if (warp == 0) {
         // ---------------- producer
         if (lane != 0) return;
         unsigned it = 0;
         bool ok = true;
+        const bool skip_first = inject_us > 0 && blockIdx.x == 0;
         for (int item = blockIdx.x; item < total && ok; item += gridDim.x) {
             const int li = find_lattice(g.item_begin, n_lat, item);
             const LatDesc* dp = g.desc + li;
@@ -160,10 +166,11 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
             const T* in = static_cast<const T*>(dp->buf[dp->cur ^ (j & 1)]);
             for (int y = y0; y < y1; ++y, ++it) {
                 const int s = it % S;
-                if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1)) {
+                if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1, lim)) {
                     ok = false;
                     break;
                 }
+                if (skip_first && it == 0) continue;   // injected: this slot is never filled
                 mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
                 const int ym = (y == 0) ? ny - 1 : y - 1;
                 const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
@@ -176,12 +183,12 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
                 }
             }
         }
-        if (!ok) {
-            atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
-            // let the copies already issued land before the block exits
-            const unsigned first = it > (unsigned)S ? it - S : 0;
-            for (unsigned q = first; q < it; ++q) mbar_wait(&full[q % S], (q / S) & 1);
-        }
+        if (!ok) atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
+        // every copy issued lands before the block exits, also when the
+        // consumers stopped waiting after a timeout (bounded waits)
+        const unsigned first = it > (unsigned)S ? it - S : 0;
+        for (unsigned q = first; q < it; ++q)
+            if (!(skip_first && q == 0)) mbar_wait(&full[q % S], (q / S) & 1, lim);
         return;
     }
 
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
         }
         for (int y = y0; y < y1; ++y, ++it) {
             const int s = it % S;
-            if (!dead && !mbar_wait(&full[s], (it / S) & 1)) {
+            if (!dead && !mbar_wait(&full[s], (it / S) & 1, lim)) {
                 dead = true;
                 atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
             }

@@ -10,9 +10,11 @@
 
 namespace lbm {
 
-// ~1.7e7 try_wait polls (each suspends for a short, implementation-defined
-// time): far longer than any legitimate wait, far shorter than a hang.
+// A wait gives up after WAIT_NS of device time (%globaltimer) or WAIT_LIMIT
+// try_wait polls, whichever comes first: far longer than any legitimate wait
+// (microseconds), far shorter than a hang.
 constexpr unsigned WAIT_LIMIT = 1u << 24;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 // Error bits written to the group header word hdr[2].
 constexpr int ERR_WAIT_TIMEOUT = 1;
@@ -51,11 +53,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-// Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity to complete: at most
+// limit_ns of device time and WAIT_LIMIT polls. Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = WAIT_NS) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 1; i < WAIT_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 31) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 

@@ -10,6 +10,7 @@
 // then the lattice's memory is released and waiting requests are admitted.
 // Requests that arrive while others are on the GPU join at the next round,
 // so their work overlaps on the device.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -77,6 +78,8 @@ struct lbm_server {
     std::deque<uint64_t> queue;
     std::vector<uint64_t> running;
     int64_t n_done = 0;
+    std::atomic<int> inject_req{0};  // wait-timeout injection requested (microseconds, 0 = off)
+    int inject_applied = 0;          // worker thread only
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -200,7 +203,13 @@ struct lbm_server {
                 }
             }
             if (running.empty()) continue;
-            int rc = e.step(chunk);
+            int rc = LBM_OK;
+            const int want = inject_req.load();
+            if (want != inject_applied) {
+                rc = e.inject_wait_timeout(want);
+                inject_applied = want;
+            }
+            if (rc == LBM_OK) rc = e.step(chunk);
             if (rc == LBM_OK) rc = e.sync();
             std::vector<uint64_t> still;
             for (uint64_t t : running) {
@@ -328,6 +337,15 @@ int lbm_cancel(lbm_server* s, uint64_t ticket) {
     } else if (q.state == 1) {
         q.cancel = true;
     }
+    return LBM_OK;
+}
+
+int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds) {
+    if (!s || microseconds < 0 || microseconds > 1000000) {
+        lbm::set_error("wait-timeout injection takes 0 (off) to 1e6 microseconds");
+        return LBM_EINVAL;
+    }
+    s->inject_req.store(microseconds);
     return LBM_OK;
 }
 

@@ -92,6 +92,9 @@ _SIGS = [
     ("lbm_destroy", None, [_P]),
     ("lbm_get_spec", _i, [_P, ctypes.POINTER(lbm_spec)]),
     ("lbm_set_weno_eps", _i, [_P, _d]),
+    ("lbm_inject_wait_timeout", _i, [_P, _i]),
+    ("lbm_batch_inject_wait_timeout", _i, [_P, _i]),
+    ("lbm_server_inject_wait_timeout", _i, [_P, _i]),
     ("lbm_init", _i, [_P, _D, _D, _D]),
     ("lbm_set_populations", _i, [_P, _D]),
     ("lbm_step", _i, [_P, _i64]),
@@ -288,6 +291,10 @@ class Lattice:
     def set_weno_eps(self, eps):
         check(lib().lbm_set_weno_eps(self._h, eps), "lbm_set_weno_eps")
 
+    def inject_wait_timeout(self, microseconds):
+        """Test injection: the next CS bulk-copy launches run a wait out (see lbm.h)."""
+        check(lib().lbm_inject_wait_timeout(self._h, int(microseconds)), "lbm_inject_wait_timeout")
+
     def init(self, rho, ux, uy):
         shp = (self.ny, self.nx)
         r, u, v = _f64(rho, shp), _f64(ux, shp), _f64(uy, shp)
@@ -404,6 +411,10 @@ class Batch:
 
     def step(self, n):
         check(lib().lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def inject_wait_timeout(self, microseconds):
+        """Test injection: the next CS bulk-copy launches run a wait out (see lbm.h)."""
+        check(lib().lbm_batch_inject_wait_timeout(self._h, int(microseconds)), "lbm_batch_inject_wait_timeout")
 
     def sync(self):
         check(lib().lbm_batch_sync(self._h), "lbm_batch_sync")
@@ -540,6 +551,10 @@ class Server:
 
     def cancel(self, ticket):
         check(lib().lbm_cancel(self._h, ticket), "lbm_cancel")
+
+    def inject_wait_timeout(self, microseconds):
+        """Test injection from the next round on (see lbm.h)."""
+        check(lib().lbm_server_inject_wait_timeout(self._h, int(microseconds)), "lbm_server_inject_wait_timeout")
 
     def drain(self, timeout_s=600.0):
         check(lib().lbm_server_drain(self._h, timeout_s), "lbm_server_drain")
