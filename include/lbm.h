@@ -84,13 +84,22 @@ typedef struct {
     int32_t reserved;
 } lbm_obs;
 
+/* State storage of a CS lattice. LBM_STORE_AB: two buffers, pull form.
+ * LBM_STORE_INPLACE: one buffer updated in place (the AA access pattern:
+ * even steps collide at the node and write to the opposite velocity's slot,
+ * odd steps read and write the nine locations a node owns), half the device
+ * memory at the same traffic and bit-identical results. FD needs its three
+ * stage buffers: LBM_STORE_INPLACE with LBM_FD is LBM_EINVAL. */
+#define LBM_STORE_AB 0
+#define LBM_STORE_INPLACE 1
+
 /* Parameters of a lattice. See lbm_create for their meaning. */
 typedef struct {
     int model;        /* LBM_CS or LBM_FD */
     int q_per_axis;   /* 3 for CS; 3, 4 or 5 for FD */
     int nx, ny;       /* lattice nodes per axis, >= 1 */
     int precision;    /* LBM_FP64 or LBM_FP32_DEV */
-    int reserved;
+    int storage;      /* LBM_STORE_AB (0, default) or LBM_STORE_INPLACE (CS only) */
     double tau;       /* CS: tau_LU; FD: tau_FD */
     double dt;        /* time step (CS: 0 selects 1/sqrt(3)) */
     double dx;        /* node spacing (CS: 0 selects 1; FD: 0 selects 1/nx) */
@@ -230,9 +239,11 @@ int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t size);
 /* Device view of the storage, for zero-copy use (e.g. as torch tensors).
  * base points to plane 0 of the buffer that holds the current state;
  * element (k, y, x) is at base + k*plane + y*pitch + x, in float64
- * (LBM_FP64) or float32 deviations (LBM_FP32_DEV). For CS the stored phase
- * is the post-collision state shifted: f_k(x, t) = stored_k(x - c_k).
- * Valid until the next lbm_step. */
+ * (LBM_FP64) or float32 deviations (LBM_FP32_DEV). cs_pull_phase says how
+ * the populations sit in it: 0 node order, f_k(x, t) = stored_k(x) (FD, and
+ * in-place CS after an even number of steps); 1 the pull form of two-buffer
+ * CS, f_k(x, t) = stored_k(x - c_k); 2 in-place CS after an odd number of
+ * steps, f_k(x, t) = stored_{8-k}(x - c_k). Valid until the next lbm_step. */
 typedef struct {
     void* base;
     int64_t plane;

@@ -287,12 +287,11 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t size) {
 int lbm_device_view(lbm_ctx* c, lbm_view* out) {
     if (!c || !out) return LBM_EINVAL;
     lbm::Lattice& L = c->e.L(0);
-    const int b = L.spec.model == LBM_CS ? L.cur : 0;
-    out->base = L.buf[b];
+    out->base = L.buf[L.state_buf()];
     out->plane = L.plane;
     out->pitch = L.pitch;
     out->elem_bytes = L.elem;
-    out->cs_pull_phase = L.spec.model == LBM_CS ? 1 : 0;
+    out->cs_pull_phase = L.phase_code();
     out->reserved = 0;
     return LBM_OK;
 }

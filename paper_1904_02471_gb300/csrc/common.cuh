@@ -28,7 +28,8 @@ struct LatDesc {
     long long plane;        // elements per population plane
     int item_begin;         // first work item of this lattice in its group
     int items;              // number of work items
-    int cur;                // CS: index (0/1) of the buffer holding the state
+    int cur;                // CS: index (0/1) of the buffer holding the state; in place: the phase
+    int inplace;            // CS: one buffer updated in place (AA pattern)
     int obs_every;          // record observables when (step - obs_base) % obs_every == 0 (0: off)
     long long obs_base;     // step at which recording started
     long long step0;        // steps completed

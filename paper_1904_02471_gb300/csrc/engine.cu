@@ -91,7 +91,11 @@ int Engine::validate(const lbm_spec* in, lbm_spec* out) {
         }
         if (s.dt > s.tau * (1.0 + 1e-12)) { set_error("FD requires dt <= tau (non-stiff BGK term, Sec. 4.1)"); return LBM_ESTIFF; }
     }
-    s.reserved = 0;
+    if (s.storage != LBM_STORE_AB && s.storage != LBM_STORE_INPLACE) { set_error("bad storage"); return LBM_EINVAL; }
+    if (s.storage == LBM_STORE_INPLACE && s.model != LBM_CS) {
+        set_error("in-place storage is for CS lattices (FD needs its three stage buffers)");
+        return LBM_EINVAL;
+    }
     *out = s;
     return LBM_OK;
 }
@@ -158,7 +162,7 @@ size_t Engine::footprint(const lbm_spec& s) {
     const int K = s.q_per_axis * s.q_per_axis;
     const long long pitch = (s.nx + 8 + 31) / 32 * 32;
     const long long plane = pitch * s.ny;
-    const int nbuf = s.model == LBM_CS ? 2 : 3;
+    const int nbuf = s.model == LBM_CS ? (s.storage == LBM_STORE_INPLACE ? 1 : 2) : 3;
     const int elem = s.precision == LBM_FP64 ? 8 : 4;
     return (size_t)nbuf * (K * plane + Lattice::TAIL) * elem + sizeof(double) * NOBS * 1024;
 }
@@ -172,7 +176,7 @@ int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
     L.elem = s.precision == LBM_FP64 ? 8 : 4;
     L.pitch = (s.nx + 8 + 31) / 32 * 32;
     L.plane = (long long)L.pitch * s.ny;
-    L.nbuf = s.model == LBM_CS ? 2 : 3;
+    L.nbuf = s.model == LBM_CS ? (s.storage == LBM_STORE_INPLACE ? 1 : 2) : 3;
     L.rho0s = s.precision == LBM_FP64 ? 0.0 : s.rho0;
     if (s.model == LBM_CS) {
         L.omega = s.dt / s.tau;
@@ -267,6 +271,7 @@ LatDesc Engine::make_desc(const Lattice& L, const Group& g, int item_begin, doub
     d.item_begin = item_begin;
     d.items = d.tiles_x * tiles_y;
     d.cur = L.cur;
+    d.inplace = L.inplace() ? 1 : 0;
     d.obs_every = (int)L.obs_every;
     d.obs_base = L.obs_base;
     d.step0 = L.step0;
@@ -824,6 +829,7 @@ struct CkptHeader {
     int64_t step0;
     int64_t eps_bits;
     int64_t state_bytes;
+    int64_t phase;   // in-place CS: phase of the stored state
 };
 
 size_t Engine::checkpoint_size(int i) const {
@@ -836,14 +842,15 @@ int Engine::save(int i, void* buf, size_t size) {
     Lattice& L = lat[i];
     CkptHeader h;
     memset(&h, 0, sizeof h);
-    memcpy(h.magic, "LBMCKPT1", 8);
+    memcpy(h.magic, "LBMCKPT2", 8);
     h.spec = L.spec;
     h.step0 = L.step0;
     memcpy(&h.eps_bits, &L.eps, 8);
     h.state_bytes = (int64_t)L.K * L.plane * L.elem;
+    h.phase = L.inplace() ? L.cur : 0;
     memcpy(buf, &h, sizeof h);
-    const int b = L.spec.model == LBM_CS ? L.cur : 0;
-    CK(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h, L.buf[b], h.state_bytes, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h, L.buf[L.state_buf()], h.state_bytes, cudaMemcpyDeviceToHost,
+                       stream_));
     CK(cudaStreamSynchronize(stream_));
     return LBM_OK;
 }
@@ -853,14 +860,14 @@ int Engine::load(int i, const void* buf, size_t size) {
     Lattice& L = lat[i];
     CkptHeader h;
     memcpy(&h, buf, sizeof h);
-    if (memcmp(h.magic, "LBMCKPT1", 8) != 0 || memcmp(&h.spec, &L.spec, sizeof(lbm_spec)) != 0 ||
+    if (memcmp(h.magic, "LBMCKPT2", 8) != 0 || memcmp(&h.spec, &L.spec, sizeof(lbm_spec)) != 0 ||
         h.state_bytes != (int64_t)L.K * L.plane * L.elem || size < checkpoint_size(i)) {
         set_error("checkpoint does not match this lattice");
         return LBM_EINVAL;
     }
     CK(cudaStreamSynchronize(stream_));
     CK(cudaMemcpyAsync(L.buf[0], static_cast<const char*>(buf) + sizeof h, h.state_bytes, cudaMemcpyHostToDevice, stream_));
-    L.cur = 0;
+    L.cur = L.inplace() ? (int)(h.phase & 1) : 0;
     L.step0 = h.step0;
     memcpy(&L.eps, &h.eps_bits, 8);
     L.obs_base = L.step0;

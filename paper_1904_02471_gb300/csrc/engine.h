@@ -34,7 +34,12 @@ struct Lattice {
     // host mirror of the device-side dynamic state
     long long step0 = 0;
     long long remaining = UNLIMITED;
-    int cur = 0;
+    int cur = 0;             // CS: buffer holding the state (two buffers) or phase (in place)
+    bool inplace() const { return spec.model == LBM_CS && spec.storage == LBM_STORE_INPLACE; }
+    // buffer that holds the current state
+    int state_buf() const { return spec.model == LBM_CS && !inplace() ? cur : 0; }
+    // lbm_view::cs_pull_phase of the current state
+    int phase_code() const { return spec.model != LBM_CS ? 0 : (!inplace() ? 1 : (cur ? 2 : 0)); }
     // observables
     int probe_comp = -1;
     double probe_norm = 0;

@@ -16,10 +16,93 @@
 // values: rho = rho0 + sum s_k, j = sum s_k v_k (sum w_k v_k = 0), and the
 // stored equilibrium is w_k [ (rho - rho0) + rho (xi + (xi^2 - u^2)/2) ],
 // xi = v_k . u, i.e. Eq. (herfeq) minus w_k rho0 (Sec. 2).
+//
+// In-place storage (one buffer, the AA access pattern): steps alternate.
+//   even step, state in node order (slot k at x holds f_k(x)): collide at x
+//     and write f*_k to slot 8 - k (the opposite velocity, k = ix + 3 iy) at x;
+//   odd step, state as the even step left it (f_k(x) is in slot 8 - k at
+//     x - c_k): read there, collide, write f*_k to slot k at x + c_k, which
+//     leaves the state in node order again.
+// In both steps a node reads and writes the same nine locations and no other
+// node touches them, so the update needs no second buffer and has no races.
+// Which step a lattice takes is its phase bit (LatDesc::cur) flipped every
+// step, so lattices of either storage and phase share a launch.
 #include "kernels.h"
 #include "ptx.cuh"
 
 namespace lbm {
+
+enum { CS_AB = 0, CS_AA_EVEN = 1, CS_AA_ODD = 2 };
+
+__device__ __forceinline__ int cs_mode(const LatDesc& d, int j) {
+    const int ph = d.cur ^ (j & 1);
+    return d.inplace ? (ph ? CS_AA_ODD : CS_AA_EVEN) : CS_AB;
+}
+
+// In-place rows of the plain kernel (see above); buf is the one state buffer.
+template <typename T, int RY, int MODE>
+__device__ __forceinline__ void cs_plain_aa_rows(const LatDesc* dp, T* buf, int x, int by, T omega, T r0, bool obs,
+                                                 int pc, T pxv, T (&acc)[NOBS]) {
+    const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
+    const long long plane = dp->plane;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x + 1 >= nx) ? x + 1 - nx : x + 1;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const int y = by * RY + r;
+        if (y >= ny) break;
+        const int ym = (y == 0) ? ny - 1 : y - 1;
+        const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+        const long long rowm = (long long)ym * pitch, row0 = (long long)y * pitch, rowp = (long long)yp * pitch;
+        T s[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+            if (MODE == CS_AA_EVEN) {
+                s[k] = buf[k * plane + row0 + x];
+            } else {
+                const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+                const long long sr = cy == 1 ? rowm : (cy == -1 ? rowp : row0);
+                s[k] = buf[(8 - k) * plane + sr + sx];
+            }
+        }
+        T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            dr += s[k];
+            if (vx_of<3>(k) != 0.0) jx += s[k] * (T)vx_of<3>(k);
+            if (vy_of<3>(k) != 0.0) jy += s[k] * (T)vy_of<3>(k);
+        }
+        const T rho = r0 + dr;
+        const T inv = T(1) / rho;
+        const T ux = jx * inv, uy = jy * inv;
+        const T usq = ux * ux + uy * uy;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
+            const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+            const T v = s[k] - omega * (s[k] - geq);
+            const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+            if (MODE == CS_AA_EVEN) {
+                buf[(8 - k) * plane + row0 + x] = v;
+            } else {
+                const int dxx = cx == 1 ? xp : (cx == -1 ? xm : x);
+                const long long drw = cy == 1 ? rowp : (cy == -1 ? rowm : row0);
+                buf[k * plane + drw + dxx] = v;
+            }
+        }
+        if (obs) {
+            acc[0] += dr;
+            acc[1] += jx;
+            acc[2] += jy;
+            if (pc >= 0) {
+                T pyv;
+                if constexpr (sizeof(T) == 4) pyv = dp->probe_pyf[y]; else pyv = (T)dp->probe_py[y];
+                acc[3] += (pc == 0 ? ux : uy) * pxv * pyv;
+            }
+        }
+    }
+}
 
 template <typename T, int TX, int RY>
 __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
@@ -34,7 +117,7 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
         const long long plane = dp->plane;
         const int local = item - dp->item_begin;
         const int bx = local % dp->tiles_x, by = local / dp->tiles_x;
-        const int cur = dp->cur ^ (j & 1);
+        const int cur = dp->cur ^ (j & 1);   // A/B storage: the buffer holding the state
         const T* __restrict__ in = static_cast<const T*>(dp->buf[cur]);
         T* __restrict__ out = static_cast<T*>(dp->buf[cur ^ 1]);
         const T omega = lat_val<T>(dp->omega, dp->omega_f);
@@ -44,7 +127,20 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
         T acc[NOBS] = {T(0), T(0), T(0), T(0)};
 
         const int x = bx * TX + threadIdx.x;
-        if (x < nx) {
+        const int mode = cs_mode(*dp, j);
+        if (mode != CS_AB) {
+            if (x < nx) {
+                T pxv = T(0);
+                if (obs && pc >= 0) {
+                    if constexpr (sizeof(T) == 4) pxv = dp->probe_pxf[x]; else pxv = (T)dp->probe_px[x];
+                }
+                T* buf = static_cast<T*>(dp->buf[0]);
+                if (mode == CS_AA_EVEN)
+                    cs_plain_aa_rows<T, RY, CS_AA_EVEN>(dp, buf, x, by, omega, r0, obs, pc, pxv, acc);
+                else
+                    cs_plain_aa_rows<T, RY, CS_AA_ODD>(dp, buf, x, by, omega, r0, obs, pc, pxv, acc);
+            }
+        } else if (x < nx) {
             const int xm = (x == 0) ? nx - 1 : x - 1;
             const int xp = (x + 1 >= nx) ? x + 1 - nx : x + 1;
             T pxv = T(0);
@@ -121,8 +217,133 @@ __host__ __device__ constexpr size_t cs_bulk_smem() {
     return (size_t)S * 9 * (W + 8) * sizeof(T) + 2 * S * sizeof(uint64_t) + (W / 32) * NOBS * sizeof(double);
 }
 
+// Producer: issue the row copies of one work item (rows y0 .. y1-1) into the
+// ring. Slot row k holds what the consumers gather for population k: two
+// buffers, plane k at row y - c_ky; in place, even step: plane k at row y;
+// odd step: plane 8 - k at row y - c_ky. Returns false when a wait ran out.
+template <typename T, int W, int S, int MODE>
+__device__ __forceinline__ bool cs_bulk_issue(T* ring, uint64_t* full, uint64_t* empty, const T* in, long long plane,
+                                              int pitch, int ny, int x0, int y0, int y1, unsigned& it, bool skip_first,
+                                              unsigned long long lim) {
+    constexpr int SEG = W + 8;
+    constexpr unsigned SEG_BYTES = SEG * sizeof(T);
+    constexpr unsigned SLOT_BYTES = 9 * SEG_BYTES;
+    for (int y = y0; y < y1; ++y, ++it) {
+        const int s = it % S;
+        if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1, lim)) return false;
+        if (skip_first && it == 0) continue;   // injected: this slot is never filled
+        mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
+        const int ym = (y == 0) ? ny - 1 : y - 1;
+        const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int cy = c3_of(k / 3);
+            const int sy = MODE == CS_AA_EVEN ? y : (cy == 1 ? ym : (cy == -1 ? yp : y));
+            const int sp = MODE == CS_AA_ODD ? 8 - k : k;
+            bulk_g2s(ring + ((size_t)s * 9 + k) * SEG, in + sp * plane + (long long)sy * pitch + x0 - 4, SEG_BYTES,
+                     &full[s]);
+        }
+    }
+    return true;
+}
+
+// Consumers: collide the rows of one work item from the ring and store (two
+// buffers: to the other buffer at x; in place, even: to slot 8 - k at x; odd:
+// to slot k at x + c_k). `in` and `out` are the same buffer in place: every
+// node reads its nine locations (from shared memory, or for the periodic x
+// wrap from global memory) before it writes them.
+template <typename T, int W, int S, int MODE>
+__device__ __forceinline__ void cs_bulk_consume(const T* ring, uint64_t* full, uint64_t* empty, const T* in_, T* out_,
+                                                const LatDesc* dp, int x0, int y0, int y1, T omega, T r0, bool obs,
+                                                T pxv, unsigned& it, bool& dead, int* err, unsigned long long lim,
+                                                T (&acc)[NOBS]) {
+    constexpr int SEG = W + 8;
+    const T* __restrict__ in = in_;
+    T* __restrict__ out = out_;
+    const int ctid = threadIdx.x - 32, lane = threadIdx.x & 31;
+    const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
+    const long long plane = dp->plane;
+    const int pc = dp->probe_comp;
+    const int x = x0 + ctid;
+    const bool xin = x < nx;
+    for (int y = y0; y < y1; ++y, ++it) {
+        const int s = it % S;
+        if (!dead && !mbar_wait(&full[s], (it / S) & 1, lim)) {
+            dead = true;
+            atomicOr(err, ERR_WAIT_TIMEOUT);
+        }
+        if (!dead && xin) {
+            const T* slot = ring + (size_t)s * 9 * SEG;
+            const int ym = (y == 0) ? ny - 1 : y - 1;
+            const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+            T f[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+                if (MODE == CS_AA_EVEN) {
+                    f[k] = slot[k * SEG + ctid + 4];
+                } else {
+                    f[k] = slot[k * SEG + ctid + 4 - cx];
+                    if ((cx == 1 && x == 0) || (cx == -1 && x == nx - 1)) {
+                        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                        const int sp = MODE == CS_AA_ODD ? 8 - k : k;
+                        f[k] = in[sp * plane + (long long)sy * pitch + (cx == 1 ? nx - 1 : 0)];
+                    }
+                }
+            }
+            T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                dr += f[k];
+                if (vx_of<3>(k) != 0.0) jx += f[k] * (T)vx_of<3>(k);
+                if (vy_of<3>(k) != 0.0) jy += f[k] * (T)vy_of<3>(k);
+            }
+            const T rho = r0 + dr;
+            const T inv = T(1) / rho;
+            const T ux = jx * inv, uy = jy * inv;
+            const T usq = ux * ux + uy * uy;
+            const long long row0 = (long long)y * pitch + x;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
+                const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
+                const T v = f[k] - omega * (f[k] - geq);
+                if (MODE == CS_AB) {
+                    __stcs(out + k * plane + row0, v);
+                } else if (MODE == CS_AA_EVEN) {
+                    __stcs(out + (8 - k) * plane + row0, v);
+                } else {
+                    const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+                    const int dxx = cx == 1 ? (x + 1 >= nx ? 0 : x + 1) : (cx == -1 ? (x == 0 ? nx - 1 : x - 1) : x);
+                    const int dyy = cy == 1 ? yp : (cy == -1 ? ym : y);
+                    __stcs(out + k * plane + (long long)dyy * pitch + dxx, v);
+                }
+            }
+            if (obs) {
+                acc[0] += dr;
+                acc[1] += jx;
+                acc[2] += jy;
+                if (pc >= 0) {
+                    T pyv;
+                    if constexpr (sizeof(T) == 4) pyv = dp->probe_pyf[y]; else pyv = (T)dp->probe_py[y];
+                    acc[3] += (pc == 0 ? ux : uy) * pxv * pyv;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && !dead) mbar_arrive(&empty[s]);
+    }
+}
+
+// Resident blocks per SM the register allocation is bounded for: the
+// blocks the shared-memory ring allows (FP32: 4 of 38 KiB at W = 256, 6 at
+// W = 128; FP64: 2 and 3), so that the bytes in flight, not registers, set
+// the occupancy (about 56 registers per thread for FP32).
+template <typename T, int W>
+constexpr int cs_bulk_min_blocks() { return sizeof(T) == 4 ? (W == 256 ? 4 : 6) : (W == 256 ? 2 : 3); }
+
 template <typename T, int W, int RB, int S>
-__global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
+__global__ void __launch_bounds__(32 + W, cs_bulk_min_blocks<T, W>()) cs_bulk_kernel(GroupDev g, int j) {
     constexpr int NCW = W / 32;
     constexpr int SEG = W + 8;
     constexpr unsigned SEG_BYTES = SEG * sizeof(T);
@@ -163,25 +384,16 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
             const int bx = local % dp->tiles_x, by = local / dp->tiles_x;
             const int x0 = bx * W, y0 = by * RB;
             const int y1 = min(y0 + RB, ny);
-            const T* in = static_cast<const T*>(dp->buf[dp->cur ^ (j & 1)]);
-            for (int y = y0; y < y1; ++y, ++it) {
-                const int s = it % S;
-                if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1, lim)) {
-                    ok = false;
-                    break;
-                }
-                if (skip_first && it == 0) continue;   // injected: this slot is never filled
-                mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
-                const int ym = (y == 0) ? ny - 1 : y - 1;
-                const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const int cy = c3_of(k / 3);
-                    const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-                    bulk_g2s(ring + ((size_t)s * 9 + k) * SEG, in + k * plane + (long long)sy * pitch + x0 - 4, SEG_BYTES,
-                             &full[s]);
-                }
-            }
+            const int mode = cs_mode(*dp, j);
+            const T* in = static_cast<const T*>(dp->buf[mode == CS_AB ? dp->cur ^ (j & 1) : 0]);
+            if (mode == CS_AB)
+                ok = cs_bulk_issue<T, W, S, CS_AB>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it, skip_first, lim);
+            else if (mode == CS_AA_EVEN)
+                ok = cs_bulk_issue<T, W, S, CS_AA_EVEN>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
+                                                        skip_first, lim);
+            else
+                ok = cs_bulk_issue<T, W, S, CS_AA_ODD>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
+                                                       skip_first, lim);
         }
         if (!ok) atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
         // every copy issued lands before the block exits, also when the
@@ -200,78 +412,34 @@ __global__ void __launch_bounds__(32 + W) cs_bulk_kernel(GroupDev g, int j) {
         const int li = find_lattice(g.item_begin, n_lat, item);
         const LatDesc* dp = g.desc + li;
         if ((long long)j >= dp->remaining) continue;
-        const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
-        const long long plane = dp->plane;
+        const int nx = dp->nx, ny = dp->ny;
         const int local = item - dp->item_begin;
         const int bx = local % dp->tiles_x, by = local / dp->tiles_x;
         const int x0 = bx * W, y0 = by * RB;
         const int y1 = min(y0 + RB, ny);
+        const int mode = cs_mode(*dp, j);
         const int cur = dp->cur ^ (j & 1);
-        const T* __restrict__ in = static_cast<const T*>(dp->buf[cur]);
-        T* __restrict__ out = static_cast<T*>(dp->buf[cur ^ 1]);
+        const T* in = static_cast<const T*>(dp->buf[mode == CS_AB ? cur : 0]);
+        T* out = static_cast<T*>(dp->buf[mode == CS_AB ? cur ^ 1 : 0]);
         const T omega = lat_val<T>(dp->omega, dp->omega_f);
         const T r0 = lat_val<T>(dp->rho0, dp->rho0_f);
         const bool obs = observe_now(*dp, j);
         const int pc = dp->probe_comp;
         const int x = x0 + ctid;
-        const bool xin = x < nx;
         T acc[NOBS] = {T(0), T(0), T(0), T(0)};
         T pxv = T(0);
-        if (obs && pc >= 0 && xin) {
+        if (obs && pc >= 0 && x < nx) {
             if constexpr (sizeof(T) == 4) pxv = dp->probe_pxf[x]; else pxv = (T)dp->probe_px[x];
         }
-        for (int y = y0; y < y1; ++y, ++it) {
-            const int s = it % S;
-            if (!dead && !mbar_wait(&full[s], (it / S) & 1, lim)) {
-                dead = true;
-                atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);
-            }
-            if (!dead && xin) {
-                const T* slot = ring + (size_t)s * 9 * SEG;
-                const int ym = (y == 0) ? ny - 1 : y - 1;
-                const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
-                T f[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const int cx = c3_of(k % 3), cy = c3_of(k / 3);
-                    f[k] = slot[k * SEG + ctid + 4 - cx];
-                    if ((cx == 1 && x == 0) || (cx == -1 && x == nx - 1)) {
-                        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-                        f[k] = in[k * plane + (long long)sy * pitch + (cx == 1 ? nx - 1 : 0)];
-                    }
-                }
-                T dr = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    dr += f[k];
-                    if (vx_of<3>(k) != 0.0) jx += f[k] * (T)vx_of<3>(k);
-                    if (vy_of<3>(k) != 0.0) jy += f[k] * (T)vy_of<3>(k);
-                }
-                const T rho = r0 + dr;
-                const T inv = T(1) / rho;
-                const T ux = jx * inv, uy = jy * inv;
-                const T usq = ux * ux + uy * uy;
-                const long long row0 = (long long)y * pitch + x;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
-                    const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
-                    __stcs(out + k * plane + row0, f[k] - omega * (f[k] - geq));
-                }
-                if (obs) {
-                    acc[0] += dr;
-                    acc[1] += jx;
-                    acc[2] += jy;
-                    if (pc >= 0) {
-                        T pyv;
-                        if constexpr (sizeof(T) == 4) pyv = dp->probe_pyf[y]; else pyv = (T)dp->probe_py[y];
-                        acc[3] += (pc == 0 ? ux : uy) * pxv * pyv;
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0 && !dead) mbar_arrive(&empty[s]);
-        }
+        if (mode == CS_AB)
+            cs_bulk_consume<T, W, S, CS_AB>(ring, full, empty, in, out, dp, x0, y0, y1, omega, r0, obs, pxv, it, dead,
+                                            g.hdr + 2, lim, acc);
+        else if (mode == CS_AA_EVEN)
+            cs_bulk_consume<T, W, S, CS_AA_EVEN>(ring, full, empty, in, out, dp, x0, y0, y1, omega, r0, obs, pxv, it,
+                                                 dead, g.hdr + 2, lim, acc);
+        else
+            cs_bulk_consume<T, W, S, CS_AA_ODD>(ring, full, empty, in, out, dp, x0, y0, y1, omega, r0, obs, pxv, it,
+                                                dead, g.hdr + 2, lim, acc);
         if (obs) {
             T r[NOBS];
 #pragma unroll

@@ -1,10 +1,12 @@
 // State initialisation, readout and observables reductions.
 //
-// CS lattices are stored in the pull phase: stored_k(m) = f*_k(m, t-1), the
-// post-collision value at m that streams to m + c_k, so the pre-collision
-// state of Eq. (sc_evolution) is f_k(x, t) = stored_k(x - c_k). Writing a
-// state f therefore stores f_k(x) at x - c_k; reading gathers from x - c_k.
-// FD lattices store f^n as is. Deviation storage adds / removes w_k rho0.
+// CS lattices with two buffers are stored in the pull phase: stored_k(m) =
+// f*_k(m, t-1), the post-collision value at m that streams to m + c_k, so the
+// pre-collision state of Eq. (sc_evolution) is f_k(x, t) = stored_k(x - c_k).
+// Writing a state f therefore stores f_k(x) at x - c_k; reading gathers from
+// x - c_k. In-place CS lattices (one buffer) hold f_k(x) at plane k, node x
+// after an even number of steps and at plane 8 - k, node x - c_k after an odd
+// number. FD lattices store f^n as is. Deviation storage adds / removes w_k rho0.
 //
 // Global sums (mass, momentum, probe amplitude) are float64 from the first
 // addition on here, reduced block-wise into partials and then in a fixed
@@ -18,6 +20,19 @@ __device__ __forceinline__ int lat_c(int i) {
     return Q1 == 3 ? c3_of(i) : 0;
 }
 
+// Where f_k(x) of a lattice is stored: buffer, shift by -c_k, mirrored plane.
+struct StoreMap {
+    int buf;
+    bool shift;
+    bool mirror;
+};
+template <bool PULL>
+__device__ __forceinline__ StoreMap store_map(const LatDesc* d) {
+    if (!PULL) return {0, false, false};               // FD: node order
+    if (!d->inplace) return {d->cur, true, false};     // two-buffer CS: pull form
+    return {0, d->cur != 0, d->cur != 0};              // in-place CS, by phase
+}
+
 template <typename T, int Q1, bool PULL>
 __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* __restrict__ rho,
                                const double* __restrict__ ux, const double* __restrict__ uy) {
@@ -25,7 +40,8 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    T* __restrict__ out = static_cast<T*>(d->buf[PULL ? d->cur : 0]);
+    const StoreMap m = store_map<PULL>(d);
+    T* __restrict__ out = static_cast<T*>(d->buf[m.buf]);
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
@@ -37,13 +53,13 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
             // Eq. (herfeq) minus the storage offset w_k rho0
             const double dev = w_of<Q1>(k) * ((r - r0) + r * (xi + 0.5 * (xi * xi - usq)));
             int xd = x, yd = y;
-            if (PULL) {
+            if (m.shift) {
                 xd = x - lat_c<Q1>(k % Q1);
                 yd = y - lat_c<Q1>(k / Q1);
                 xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
                 yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
             }
-            out[k * plane + (long long)yd * pitch + xd] = (T)dev;
+            out[(m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd] = (T)dev;
         }
     }
 }
@@ -54,20 +70,21 @@ __global__ void set_pop_kernel(const LatDesc* d, int nx, int ny, const double* _
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    T* __restrict__ out = static_cast<T*>(d->buf[PULL ? d->cur : 0]);
+    const StoreMap m = store_map<PULL>(d);
+    T* __restrict__ out = static_cast<T*>(d->buf[m.buf]);
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int xd = x, yd = y;
-            if (PULL) {
+            if (m.shift) {
                 xd = x - lat_c<Q1>(k % Q1);
                 yd = y - lat_c<Q1>(k / Q1);
                 xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
                 yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
             }
-            out[k * plane + (long long)yd * pitch + xd] = (T)(f[k * n + c] - w_of<Q1>(k) * r0);
+            out[(m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd] = (T)(f[k * n + c] - w_of<Q1>(k) * r0);
         }
     }
 }
@@ -84,7 +101,8 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    const T* __restrict__ in = static_cast<const T*>(d->buf[PULL ? d->cur : 0]);
+    const StoreMap m = store_map<PULL>(d);
+    const T* __restrict__ in = static_cast<const T*>(d->buf[m.buf]);
     const int pc = d->probe_comp;
     const long long n = (long long)wx * wy;
     double acc[NOBS] = {0.0, 0.0, 0.0, 0.0};
@@ -96,13 +114,13 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int xs = x, ys = y;
-            if (PULL) {
+            if (m.shift) {
                 xs = x - lat_c<Q1>(k % Q1);
                 ys = y - lat_c<Q1>(k / Q1);
                 xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
                 ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             }
-            const double s = (double)in[k * plane + (long long)ys * pitch + xs];
+            const double s = (double)in[(m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs];
             if (f) f[k * n + c] = s + w_of<Q1>(k) * r0;
             dr += s;
             jx += s * vx_of<Q1>(k);

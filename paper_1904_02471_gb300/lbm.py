@@ -35,7 +35,7 @@ class lbm_obs(ctypes.Structure):
 
 class lbm_spec(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("q_per_axis", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int), ("tau", ctypes.c_double),
+                ("precision", ctypes.c_int), ("storage", ctypes.c_int), ("tau", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dx", ctypes.c_double), ("rho0", ctypes.c_double)]
 
 
@@ -234,14 +234,17 @@ def lbm_fit_decay(t, a, t_skip=0.0):
 
 MODELS = {"cs": LBM_CS, "fd": LBM_FD}
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp32dev": LBM_FP32_DEV}
+LBM_STORE_AB, LBM_STORE_INPLACE = 0, 1
+STORAGES = {"ab": LBM_STORE_AB, "inplace": LBM_STORE_INPLACE}
 
 
-def make_spec(model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0) -> lbm_spec:
+def make_spec(model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, storage="ab") -> lbm_spec:
     s = lbm_spec()
     s.model = MODELS[model] if isinstance(model, str) else model
     s.q_per_axis = q
     s.nx, s.ny = nx, ny
     s.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+    s.storage = STORAGES[storage] if isinstance(storage, str) else storage
     s.tau, s.dt, s.dx, s.rho0 = tau, dt, dx, rho0
     return s
 
@@ -257,9 +260,9 @@ def _stream_ptr(stream):
 class Lattice:
     """One lattice context (lbm_create ... lbm_destroy)."""
 
-    def __init__(self, model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, stream=None):
+    def __init__(self, model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, stream=None, storage="ab"):
         self._h = ctypes.c_void_p()
-        spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0)
+        spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0, storage)
         check(lib().lbm_create_spec(ctypes.byref(self._h), ctypes.byref(spec), _stream_ptr(stream)), "lbm_create")
         out = lbm_spec()
         check(lib().lbm_get_spec(self._h, ctypes.byref(out)), "lbm_get_spec")

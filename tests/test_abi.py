@@ -103,6 +103,15 @@ def test_create_validation(args, code):
     assert ei.value.code == code
 
 
+@pytest.mark.parametrize("model,q,storage", [("fd", 4, "inplace"), ("cs", 3, 2), ("cs", 3, -1)])
+def test_storage_validation(model, q, storage):
+    """In-place storage is a CS option; FD keeps its three stage buffers."""
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Lattice(model, q, 32, 32, 0.5 if model == "cs" else 1e-2, 0.0 if model == "cs" else 1e-3,
+                    storage=storage)
+    assert ei.value.code == lbm.LBM_EINVAL
+
+
 def test_batch_validation_names_the_lattice():
     specs = [pkg.make_spec("cs", 3, 8, 8, 0.5), pkg.make_spec("fd", 4, 32, 32, 1e-4, 1e-3)]
     with pytest.raises(lbm.LbmError) as ei:
