@@ -161,7 +161,7 @@ def cpu_value(rates):
 # ---------------------------------------------------------------- GPU arm
 def build_batch(torch, stream):
     import paper_1904_02471_gb300 as pkg
-    specs = [pkg.make_spec("cs", 3, CS_N, CS_N, CS_TAU, 0.0, 0.0, "fp32"),
+    specs = [pkg.make_spec("cs", 3, CS_N, CS_N, CS_TAU, 0.0, 0.0, "fp32", storage="inplace"),
              pkg.make_spec("fd", 4, FD_N, FD_N, FD_TAU, FD_DT, 0.0, "fp32")]
     B = pkg.Batch(specs, stream=stream)
     fields = []
@@ -268,7 +268,8 @@ def run_gpu(args, rank, world):
         "data": "synthetic (Taylor-Green initial state, seeded generators)",
         "config": {
             "workload": WORKLOAD,
-            "cs": {"lattice": [CS_N, CS_N], "tau_lu": CS_TAU, "velocities": 9},
+            "cs": {"lattice": [CS_N, CS_N], "tau_lu": CS_TAU, "velocities": 9,
+                   "storage": "in place (one buffer, AA access pattern)"},
             "fd": {"lattice": [FD_N, FD_N], "tau_fd": FD_TAU, "dt_fd": FD_DT, "velocities": 16,
                    "scheme": "WENO-5 + SSP-RK3, 3 stage launches"},
             "observables": "fused float64 mass/momentum/amplitude every step",
@@ -315,13 +316,13 @@ def run_gpu(args, rank, world):
 
 # ---------------------------------------------------------------- batched + served
 def _instance_spec(pkg, d, prec):
-    """Spec of one batched/served instance: CS D2Q9 with tau_LU = tau*/sqrt 3,
-    or FD 16-velocity with tau_FD from Eq. (nu-transfer) and the largest
-    stable time step (CFL and dt <= tau)."""
+    """Spec of one batched/served instance: CS D2Q9 with tau_LU = tau*/sqrt 3
+    (FP32: in-place storage), or FD 16-velocity with tau_FD from Eq.
+    (nu-transfer) and the largest stable time step (CFL and dt <= tau)."""
     n = d["n"]
     tau_lu = d["tau_star"] / math.sqrt(3.0)
     if d["model"] == "cs":
-        return pkg.make_spec("cs", 3, n, n, tau_lu, 0.0, 0.0, prec)
+        return pkg.make_spec("cs", 3, n, n, tau_lu, 0.0, 0.0, prec, storage="inplace" if prec == "fp32" else "ab")
     tau_fd = pkg.lbm_tau_fd_from_lu(n, tau_lu)
     return pkg.make_spec("fd", 4, n, n, tau_fd, fd_dt(pkg, 4, n, tau_fd), 0.0, prec)
 
@@ -392,7 +393,7 @@ def run_batched(torch, steps=192, plain_steps=2):
     mlups_p = work / t_plain / 1e6
     return {
         "workload": "256 lattices, sides uniform in {32,64,128,256,512}, tau* U[0.51,2], half CS D2Q9 / half FD "
-                    "16-velocity, shear-wave and Taylor-Green initial states (seed 0)",
+                    "16-velocity, shear-wave and Taylor-Green initial states (seed 0); FP32 CS in place",
         "cells": cells,
         "fp32_batched": {"mlups": round(mlups_b, 1), "steps": steps, "s": round(t_b, 4), "tuning": tune.strip()},
         "fp64_plain_one_at_a_time": {
@@ -436,7 +437,8 @@ def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=
     ok = sum(1 for x in res if x["status"] == 0)
     return {
         "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{duration_s:.0f} s, CS or FD 16-velocity "
-                    f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2), steps U[{steps[0]},{steps[1]}], FP32",
+                    f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2), steps U[{steps[0]},{steps[1]}], FP32 "
+                    "(CS in place)",
         "requests": n_req, "completed_ok": ok,
         "aggregate_mlups": round(work / makespan / 1e6, 1),
         "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4), "p99": round(float(np.percentile(lat, 99)), 4),

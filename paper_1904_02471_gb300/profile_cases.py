@@ -1,6 +1,6 @@
 """Small single-lattice cases for kernel profiling (e.g. under Nsight Compute).
 
-    python -m paper_1904_02471_gb300.profile_cases cs  [--n 2048] [--steps 4] [--tile 5] [--grid G]
+    python -m paper_1904_02471_gb300.profile_cases cs  [--n 2048] [--steps 4] [--tile 5] [--grid G] [--storage inplace]
     python -m paper_1904_02471_gb300.profile_cases fd  [--n 1024] [--steps 2] [--tile 0] [--q 4] [--grid G]
 
 Each case is a Taylor-Green lattice in FP32 deviation storage whose state is
@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--q", type=int, default=4)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--storage", default="ab", choices=["ab", "inplace"])
     a = ap.parse_args()
 
     import torch
@@ -34,7 +35,7 @@ def main():
     torch.cuda.init()
     if a.model == "cs":
         n = a.n or 2048
-        L = pkg.Lattice("cs", 3, n, n, 0.8 / math.sqrt(3), precision=a.precision)
+        L = pkg.Lattice("cs", 3, n, n, 0.8 / math.sqrt(3), precision=a.precision, storage=a.storage)
         if a.tile >= 0:
             L.config(a.tile, a.grid)
         L.init(*wl.taylor_green(n, n, 0.01 * math.sqrt(3)))

@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (the same two-lattice batch, autotuned the same way): CS D2Q9 8192^2
-and FD 16-velocity 4096^2, FP32 deviation storage.
+(in-place storage) and FD 16-velocity 4096^2, FP32 deviation storage.
 
 The oracle cannot step these lattices whole, so it checks sampled windows:
 the state at step t is read in a W x W window (periodic, so windows at the
@@ -34,7 +34,7 @@ def batch():
     build.build()
     torch.cuda.init()
     cs, fd = wl.CS_ROOFLINE, wl.FD_ROOFLINE
-    specs = [pkg.make_spec("cs", 3, cs["nx"], cs["ny"], cs["tau"], 0.0, 0.0, "fp32"),
+    specs = [pkg.make_spec("cs", 3, cs["nx"], cs["ny"], cs["tau"], 0.0, 0.0, "fp32", storage="inplace"),
              pkg.make_spec("fd", 4, fd["nx"], fd["ny"], fd["tau"], fd["dt"], 0.0, "fp32")]
     B = pkg.Batch(specs)
     for i, c in enumerate((cs, fd)):
