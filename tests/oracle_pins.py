@@ -215,6 +215,66 @@ def _shear_amplitude_linear(step_matrix, vx, vy, w, U, axis, steps):
     return np.array(out)
 
 
+def _cs_exact_rational(f, omega, steps):
+    """Brute-force D2Q9 collide + stream in exact rational arithmetic, lattice
+    units (c in {-1, 0, 1}, w = (2/3, 1/6, 1/6) per axis, cs^2 = 1/3):
+    f_k(x + c_k, t + 1) = f_k - omega (f_k - w_k rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2)).
+    Written out here, independently of the oracle."""
+    from fractions import Fraction as Fr
+    K, ny, nx = len(f), len(f[0]), len(f[0][0])
+    w1 = {-1: Fr(1, 6), 0: Fr(2, 3), 1: Fr(1, 6)}
+    cs = [(k % 3 - 1, k // 3 - 1) for k in range(9)]
+    for _ in range(steps):
+        new = [[[None] * nx for _ in range(ny)] for _ in range(K)]
+        for y in range(ny):
+            for x in range(nx):
+                fk = [f[k][y][x] for k in range(9)]
+                rho = sum(fk)
+                ux = sum(fk[k] * cs[k][0] for k in range(9)) / rho
+                uy = sum(fk[k] * cs[k][1] for k in range(9)) / rho
+                usq = ux * ux + uy * uy
+                for k, (cx, cy) in enumerate(cs):
+                    cu = cx * ux + cy * uy
+                    feq = w1[cx] * w1[cy] * rho * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * usq)
+                    new[k][(y + cy) % ny][(x + cx) % nx] = fk[k] - omega * (fk[k] - feq)
+        f = new
+    return f
+
+
+def check_cs_exact_rational(mutant=0):
+    """In lattice units with a rational omega the CS update is a rational map;
+    the oracle (paper units: v = sqrt3 c, u = sqrt3 u_lattice, the same
+    populations) agrees with the exact result to rounding after 3 steps on a
+    7x5 lattice, and the exact result conserves mass exactly."""
+    from fractions import Fraction as Fr
+    nx, ny, omega = 7, 5, Fr(3, 4)
+    rho = [[1 + Fr((3 * x + 5 * y) % 7 - 3, 50) for x in range(nx)] for y in range(ny)]
+    ul = [[Fr((x + 2 * y) % 5 - 2, 100) for x in range(nx)] for y in range(ny)]
+    vl = [[Fr((3 * x + y) % 5 - 2, 100) for x in range(nx)] for y in range(ny)]
+    w1 = {-1: Fr(1, 6), 0: Fr(2, 3), 1: Fr(1, 6)}
+    f0 = []
+    for k in range(9):
+        cx, cy = k % 3 - 1, k // 3 - 1
+        plane = []
+        for y in range(ny):
+            row = []
+            for x in range(nx):
+                cu = cx * ul[y][x] + cy * vl[y][x]
+                usq = ul[y][x] ** 2 + vl[y][x] ** 2
+                row.append(w1[cx] * w1[cy] * rho[y][x] * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * usq))
+            plane.append(row)
+        f0.append(plane)
+    fe = _cs_exact_rational(f0, omega, 3)
+    assert sum(v for p in fe for r in p for v in r) == sum(v for p in f0 for r in p for v in r)
+    sq3 = math.sqrt(3.0)
+    r = np.array([[float(v) for v in row] for row in rho])
+    u = sq3 * np.array([[float(v) for v in row] for row in ul])
+    v = sq3 * np.array([[float(q) for q in row] for row in vl])
+    fo = oracle.cs_run_omega(oracle.equilibrium(3, r, u, v, mutant), float(omega), 3, mutant)
+    exact = np.array([[[float(q) for q in row] for row in p] for p in fe])
+    assert np.max(np.abs(fo - exact)) < 2e-15 * np.max(np.abs(exact)), np.max(np.abs(fo - exact))
+
+
 def check_cs_linear_modes(mutant=0):
     """Shear-wave amplitude A(t) of the oracle equals the exact linear prediction
     from the Fourier-space collide-stream matrix diag(e^{-i kappa.c_k})(I - omega(I - E))
@@ -455,6 +515,92 @@ def check_fd_linear_modes(mutant=0):
         assert rel < 1e-7, (n, rel)
 
 
+def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
+    """Brute-force FD update in mpmath, written out from the definitions:
+    Jiang-Shu WENO-5 interface values upwinded by the sign of each velocity
+    component (v = 0: no advection), conservative flux differences, BGK with
+    the moments of the stage input, SSP-RK3 in Shu-Osher form; periodic."""
+    n = len(nodes)
+    K, ny, nx = n * n, len(f[0]), len(f[0][0])
+    v = [(nodes[k % n], nodes[k // n]) for k in range(K)]
+    w = [weights[k % n] * weights[k // n] for k in range(K)]
+
+    def face(a, b, c, d, e):   # value at i+1/2 from f_{i-2..i+2}, upwind side left
+        q = [(2 * a - 7 * b + 11 * c) / 6, (-b + 5 * c + 2 * d) / 6, (2 * c + 5 * d - e) / 6]
+        beta = [mp.mpf(13) / 12 * (a - 2 * b + c) ** 2 + (a - 4 * b + 3 * c) ** 2 / 4,
+                mp.mpf(13) / 12 * (b - 2 * c + d) ** 2 + (b - d) ** 2 / 4,
+                mp.mpf(13) / 12 * (c - 2 * d + e) ** 2 + (3 * c - 4 * d + e) ** 2 / 4]
+        alpha = [dr / (eps + bt) ** 2 for dr, bt in zip((mp.mpf(1) / 10, mp.mpf(6) / 10, mp.mpf(3) / 10), beta)]
+        return sum(al * qq for al, qq in zip(alpha, q)) / sum(alpha)
+
+    def line_flux_diff(g, vel):   # (F_{i+1/2} - F_{i-1/2}) along a periodic line
+        m = len(g)
+        F = []
+        for i in range(m):   # F[i] = value at face i - 1/2
+            if vel > 0:
+                F.append(face(*[g[(i - 3 + s) % m] for s in range(5)]))
+            else:
+                F.append(face(*[g[(i + 2 - s) % m] for s in range(5)]))
+        return [F[(i + 1) % m] - F[i] for i in range(m)]
+
+    def L(g):
+        out = [[[mp.mpf(0)] * nx for _ in range(ny)] for _ in range(K)]
+        for k in range(K):
+            if v[k][0] != 0:
+                for y in range(ny):
+                    d = line_flux_diff(g[k][y], v[k][0])
+                    for x in range(nx):
+                        out[k][y][x] -= v[k][0] * d[x] / dx
+            if v[k][1] != 0:
+                for x in range(nx):
+                    d = line_flux_diff([g[k][y][x] for y in range(ny)], v[k][1])
+                    for y in range(ny):
+                        out[k][y][x] -= v[k][1] * d[y] / dx
+        for y in range(ny):
+            for x in range(nx):
+                rho = sum(g[k][y][x] for k in range(K))
+                ux = sum(g[k][y][x] * v[k][0] for k in range(K)) / rho
+                uy = sum(g[k][y][x] * v[k][1] for k in range(K)) / rho
+                usq = ux * ux + uy * uy
+                for k in range(K):
+                    xi = v[k][0] * ux + v[k][1] * uy
+                    feq = w[k] * rho * (1 + xi + xi * xi / 2 - usq / 2)
+                    out[k][y][x] -= (g[k][y][x] - feq) / tau
+        return out
+
+    def axpy(a, x, b, y):
+        return [[[a * x[k][j][i] + b * y[k][j][i] for i in range(nx)] for j in range(ny)] for k in range(K)]
+
+    for _ in range(steps):
+        f1 = axpy(1, f, dt, L(f))
+        f2 = axpy(mp.mpf(3) / 4, f, mp.mpf(1) / 4, axpy(1, f1, dt, L(f1)))
+        f = axpy(mp.mpf(1) / 3, f, mp.mpf(2) / 3, axpy(1, f2, dt, L(f2)))
+    return f
+
+
+def check_fd_high_precision(mutant=0):
+    """The oracle's FD step against a 30-digit mpmath brute force written from
+    the definitions (16 velocities with the closed-form Gauss-Hermite nodes
+    +-sqrt(3 -+ sqrt 6), weights (3 +- sqrt 6)/12; 6x6 lattice, 2 steps; a
+    rough state so that the nonlinear WENO weights are far from linear)."""
+    import mpmath as mp
+    mp.mp.dps = 30
+    s6 = mp.sqrt(6)
+    nodes = [-mp.sqrt(3 + s6), -mp.sqrt(3 - s6), mp.sqrt(3 - s6), mp.sqrt(3 + s6)]
+    weights = [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12]
+    nx = ny = 6
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=31, amp_rho=0.2, amp_u=0.1)
+    f0 = oracle.equilibrium(4, rho, ux, uy, mutant)
+    f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=32, lo=-0.2, hi=0.2))
+    dx, dt, tau, eps = 1.0 / nx, 0.02, 0.05, 1e-6
+    fm = [[[mp.mpf(float(f0[k, y, x])) for x in range(nx)] for y in range(ny)] for k in range(16)]
+    fm = _fd_mp_run(fm, nodes, weights, mp.mpf(dx), mp.mpf(dt), mp.mpf(tau), mp.mpf(eps), 2, mp)
+    exact = np.array([[[float(fm[k][y][x]) for x in range(nx)] for y in range(ny)] for k in range(16)])
+    fo = oracle.fd_run(f0, dx, dt, tau, 2, eps=eps, mutant=mutant)
+    err = np.max(np.abs(fo - exact)) / np.max(np.abs(exact))
+    assert err < 1e-13, err
+
+
 def check_fd_decay_closed_form(mutant=0):
     """FD Taylor-Green, 16 velocities, 32^2 unit domain, nu = tau_FD = 0.01
     (Eq. nu_fd): the fitted decay matches exp(-2 k^2 nu t) of Eq. (taylor)."""
@@ -556,10 +702,10 @@ ALL_CHECKS = [
     check_rule_vs_numpy, check_rule_closed_forms, check_set_moments, check_set_ordering,
     check_feq_moments, check_macro_of_equilibrium,
     check_cs_fixed_point, check_cs_streaming_direction, check_cs_periodic_return, check_cs_omega_one,
-    check_cs_conservation, check_cs_linear_modes, check_cs_decay_closed_form,
+    check_cs_conservation, check_cs_exact_rational, check_cs_linear_modes, check_cs_decay_closed_form,
     check_weno_quadratic_exact, check_weno_beta, check_weno_linear_weights, check_weno_eno,
     check_fd_linear_advection, check_fd_rk3_relaxation, check_fd_conservation, check_fd_fixed_point,
-    check_fd_linear_modes, check_fd_decay_closed_form,
+    check_fd_linear_modes, check_fd_high_precision, check_fd_decay_closed_form,
     check_units_tables, check_units_time_steps, check_shock_worked_example, check_shock_jump_conditions,
     check_cs_shock_profile,
 ]

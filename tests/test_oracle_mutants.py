@@ -10,14 +10,16 @@ import pytest
 import oracle_pins as P
 
 MUTANTS = {
-    1: ("feq: -u^2 term dropped", [P.check_feq_moments]),
-    2: ("feq: sign of v.u flipped", [P.check_feq_moments]),
-    3: ("CS: streams to x - c_k", [P.check_cs_streaming_direction]),
-    4: ("velocity components transposed", [P.check_set_ordering]),
-    5: ("WENO: mirrored third candidate", [P.check_weno_quadratic_exact]),
-    6: ("RK3: wrong second-stage weights", [P.check_fd_rk3_relaxation]),
-    7: ("WENO: downwind stencil for v > 0", [P.check_fd_linear_advection, P.check_fd_linear_modes]),
-    8: ("WENO: wrong beta_2 coefficient", [P.check_weno_beta]),
+    1: ("feq: -u^2 term dropped", [P.check_feq_moments, P.check_cs_exact_rational, P.check_fd_high_precision]),
+    2: ("feq: sign of v.u flipped", [P.check_feq_moments, P.check_cs_exact_rational, P.check_fd_high_precision]),
+    3: ("CS: streams to x - c_k", [P.check_cs_streaming_direction, P.check_cs_exact_rational]),
+    4: ("velocity components transposed", [P.check_set_ordering, P.check_cs_exact_rational,
+                                           P.check_fd_high_precision]),
+    5: ("WENO: mirrored third candidate", [P.check_weno_quadratic_exact, P.check_fd_high_precision]),
+    6: ("RK3: wrong second-stage weights", [P.check_fd_rk3_relaxation, P.check_fd_high_precision]),
+    7: ("WENO: downwind stencil for v > 0", [P.check_fd_linear_advection, P.check_fd_linear_modes,
+                                            P.check_fd_high_precision]),
+    8: ("WENO: wrong beta_2 coefficient", [P.check_weno_beta, P.check_fd_high_precision]),
 }
 
 
