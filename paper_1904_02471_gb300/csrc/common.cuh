@@ -141,9 +141,6 @@ __device__ __forceinline__ bool observe_now(const LatDesc& d, int j) {
     return s >= 0 && (s % d.obs_every) == 0 && (s / d.obs_every) < d.obs_cap;
 }
 
-// Fast reciprocal-free division where exact rounding is not required.
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 // Block reduction of NOBS per-thread partial sums into out[NOBS] (double).
 // Warp level in T (for FP32 storage: at most 32 per-thread sums in float),

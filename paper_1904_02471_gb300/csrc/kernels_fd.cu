@@ -7,14 +7,16 @@
 // One launch = one stage for every lattice of the group. The moments (rho, u)
 // and so f^eq are taken from that stage's input, as the BGK term belongs to L.
 //
-// Per tile (TX x TY nodes) and population k:
-//   1. the stage input plane k is staged in shared memory with a periodic
-//      halo of 3 nodes (the WENO-5 stencil reach),
-//   2. every interface value is computed once and stored: (TX+1) x TY faces
-//      normal to x and TX x (TY+1) normal to y (a face is shared by the two
-//      nodes it separates, which also makes the flux form conservative),
-//   3. each node takes its flux differences, adds the BGK term and combines
-//      with f^n for the stage.
+// Per tile (TX x TY nodes):
+//   1. every population plane of the stage input is staged in shared memory
+//      with a periodic halo of 3 nodes (the WENO-5 stencil reach); the
+//      moments come from there,
+//   2. per group of G populations, every interface value is computed once
+//      and stored: (TX+1) x TY faces normal to x and TX x (TY+1) normal to y
+//      (a face is shared by the two nodes it separates, which also makes the
+//      flux form conservative),
+//   3. after one barrier each node takes its flux differences, adds the BGK
+//      term and combines with f^n for the stage.
 // The WENO-5 face value is upwinded by the sign of the (constant) velocity
 // component: for v > 0 the face i+1/2 is reconstructed from f_{i-2..i+2},
 // for v < 0 from f_{i+3..i-1} (mirror image). Components equal to 0 (the
@@ -25,82 +27,10 @@
 // buf[2] = f^(2). Storage offset as in the CS kernel (deviation form for
 // FP32, full f for FP64): WENO differences and the stage combination are
 // unchanged by the constant offset w_k rho0.
-#include <type_traits>
-
 #include "kernels.h"
 #include "ptx.cuh"
 
 namespace lbm {
-
-// 1D nodes and weights, indexed [q1 - 3][i] (see GH<> in common.cuh).
-__constant__ double c_node_d[3][5] = {
-    {GH<3>::v(0), GH<3>::v(1), GH<3>::v(2), 0.0, 0.0},
-    {GH<4>::v(0), GH<4>::v(1), GH<4>::v(2), GH<4>::v(3), 0.0},
-    {GH<5>::v(0), GH<5>::v(1), GH<5>::v(2), GH<5>::v(3), GH<5>::v(4)}};
-__constant__ double c_wt_d[3][5] = {
-    {GH<3>::w(0), GH<3>::w(1), GH<3>::w(2), 0.0, 0.0},
-    {GH<4>::w(0), GH<4>::w(1), GH<4>::w(2), GH<4>::w(3), 0.0},
-    {GH<5>::w(0), GH<5>::w(1), GH<5>::w(2), GH<5>::w(3), GH<5>::w(4)}};
-__constant__ float c_node_f[3][5] = {
-    {(float)GH<3>::v(0), (float)GH<3>::v(1), (float)GH<3>::v(2), 0.f, 0.f},
-    {(float)GH<4>::v(0), (float)GH<4>::v(1), (float)GH<4>::v(2), (float)GH<4>::v(3), 0.f},
-    {(float)GH<5>::v(0), (float)GH<5>::v(1), (float)GH<5>::v(2), (float)GH<5>::v(3), (float)GH<5>::v(4)}};
-__constant__ float c_wt_f[3][5] = {
-    {(float)GH<3>::w(0), (float)GH<3>::w(1), (float)GH<3>::w(2), 0.f, 0.f},
-    {(float)GH<4>::w(0), (float)GH<4>::w(1), (float)GH<4>::w(2), (float)GH<4>::w(3), 0.f},
-    {(float)GH<5>::w(0), (float)GH<5>::w(1), (float)GH<5>::w(2), (float)GH<5>::w(3), (float)GH<5>::w(4)}};
-
-// Per-population tables (v_kx, v_ky, w_k), indexed [q1 - 3][k] for
-// k = ix + q1 * iy, so the kernels never divide by a run-time q1.
-#define LBM_KV(Q, k, F) ((k) < (Q) * (Q) ? F<Q>(k) : 0.0)
-#define LBM_KROW(Q, F)                                                                                                  \
-    {LBM_KV(Q, 0, F), LBM_KV(Q, 1, F), LBM_KV(Q, 2, F), LBM_KV(Q, 3, F), LBM_KV(Q, 4, F), LBM_KV(Q, 5, F),         \
-     LBM_KV(Q, 6, F), LBM_KV(Q, 7, F), LBM_KV(Q, 8, F), LBM_KV(Q, 9, F), LBM_KV(Q, 10, F), LBM_KV(Q, 11, F),       \
-     LBM_KV(Q, 12, F), LBM_KV(Q, 13, F), LBM_KV(Q, 14, F), LBM_KV(Q, 15, F), LBM_KV(Q, 16, F), LBM_KV(Q, 17, F),   \
-     LBM_KV(Q, 18, F), LBM_KV(Q, 19, F), LBM_KV(Q, 20, F), LBM_KV(Q, 21, F), LBM_KV(Q, 22, F), LBM_KV(Q, 23, F),   \
-     LBM_KV(Q, 24, F)}
-__constant__ double c_kvx_d[3][25] = {LBM_KROW(3, vx_of), LBM_KROW(4, vx_of), LBM_KROW(5, vx_of)};
-__constant__ double c_kvy_d[3][25] = {LBM_KROW(3, vy_of), LBM_KROW(4, vy_of), LBM_KROW(5, vy_of)};
-__constant__ double c_kw_d[3][25] = {LBM_KROW(3, w_of), LBM_KROW(4, w_of), LBM_KROW(5, w_of)};
-#define LBM_KROWF(Q, F)                                                                                                 \
-    {(float)LBM_KV(Q, 0, F), (float)LBM_KV(Q, 1, F), (float)LBM_KV(Q, 2, F), (float)LBM_KV(Q, 3, F),               \
-     (float)LBM_KV(Q, 4, F), (float)LBM_KV(Q, 5, F), (float)LBM_KV(Q, 6, F), (float)LBM_KV(Q, 7, F),               \
-     (float)LBM_KV(Q, 8, F), (float)LBM_KV(Q, 9, F), (float)LBM_KV(Q, 10, F), (float)LBM_KV(Q, 11, F),             \
-     (float)LBM_KV(Q, 12, F), (float)LBM_KV(Q, 13, F), (float)LBM_KV(Q, 14, F), (float)LBM_KV(Q, 15, F),           \
-     (float)LBM_KV(Q, 16, F), (float)LBM_KV(Q, 17, F), (float)LBM_KV(Q, 18, F), (float)LBM_KV(Q, 19, F),           \
-     (float)LBM_KV(Q, 20, F), (float)LBM_KV(Q, 21, F), (float)LBM_KV(Q, 22, F), (float)LBM_KV(Q, 23, F),           \
-     (float)LBM_KV(Q, 24, F)}
-__constant__ float c_kvx_f[3][25] = {LBM_KROWF(3, vx_of), LBM_KROWF(4, vx_of), LBM_KROWF(5, vx_of)};
-__constant__ float c_kvy_f[3][25] = {LBM_KROWF(3, vy_of), LBM_KROWF(4, vy_of), LBM_KROWF(5, vy_of)};
-__constant__ float c_kw_f[3][25] = {LBM_KROWF(3, w_of), LBM_KROWF(4, w_of), LBM_KROWF(5, w_of)};
-
-template <typename T>
-struct KTab;
-template <>
-struct KTab<double> {
-    static __device__ __forceinline__ double vx(int q1, int k) { return c_kvx_d[q1 - 3][k]; }
-    static __device__ __forceinline__ double vy(int q1, int k) { return c_kvy_d[q1 - 3][k]; }
-    static __device__ __forceinline__ double w(int q1, int k) { return c_kw_d[q1 - 3][k]; }
-};
-template <>
-struct KTab<float> {
-    static __device__ __forceinline__ float vx(int q1, int k) { return c_kvx_f[q1 - 3][k]; }
-    static __device__ __forceinline__ float vy(int q1, int k) { return c_kvy_f[q1 - 3][k]; }
-    static __device__ __forceinline__ float w(int q1, int k) { return c_kw_f[q1 - 3][k]; }
-};
-
-template <typename T>
-__device__ __forceinline__ T node1(int q1, int i);
-template <>
-__device__ __forceinline__ double node1<double>(int q1, int i) { return c_node_d[q1 - 3][i]; }
-template <>
-__device__ __forceinline__ float node1<float>(int q1, int i) { return c_node_f[q1 - 3][i]; }
-template <typename T>
-__device__ __forceinline__ T wt1(int q1, int i);
-template <>
-__device__ __forceinline__ double wt1<double>(int q1, int i) { return c_wt_d[q1 - 3][i]; }
-template <>
-__device__ __forceinline__ float wt1<float>(int q1, int i) { return c_wt_f[q1 - 3][i]; }
 
 // Pairs of values evaluated together: the x-face and the y-face of a node
 // are two independent WENO-5 reconstructions, computed side by side. For
