@@ -64,20 +64,26 @@ def kernel_digest(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link liblbm.so; returns its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+BOUNDS_DIR = os.path.join(HERE, "_build_bounds")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, bounds: bool = False) -> str:
+    """Compile and link liblbm.so; returns its path. bounds=True builds the
+    bounds-checked variant (-DLBM_BOUNDS_CHECK) into _build_bounds/ instead."""
+    out_dir = BOUNDS_DIR if bounds else OUT_DIR
+    lib_path = os.path.join(out_dir, "liblbm.so")
+    os.makedirs(out_dir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DLBM_BOUNDS_CHECK"] if bounds else [])
     digest = _digest(extra)
-    stamp = os.path.join(OUT_DIR, "liblbm.sha256")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = os.path.join(out_dir, "liblbm.sha256")
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == digest:
-                return LIB
+                return lib_path
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -92,17 +98,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if err.strip():
                 print(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(digest)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv, bounds="--bounds" in sys.argv))

@@ -53,7 +53,45 @@ struct LatDesc {
     // float copies of omega, cdx, dt_tau, rho0, eps for the FP32 kernels (a
     // conversion from double would run on the narrow FP64 pipe every tile)
     float omega_f, cdx_f, dt_tau_f, rho0_f, eps_f;
+    int* err;               // the group's error word (header word 2)
 };
+
+// State buffers: element (0, 0) of a buffer sits STATE_HEAD elements into its
+// slot of the lattice's allocation and every slot ends with STATE_TAIL spare
+// elements (row segments of bulk copies may reach into them).
+constexpr long long STATE_HEAD = 4, STATE_TAIL = 1024;
+
+// Error bit of the group error word: an access outside a state buffer caught
+// by the bounds-checked build.
+constexpr int ERR_BOUNDS = 2;
+
+// Bounds-checked build (-DLBM_BOUNDS_CHECK; compute-sanitizer stand-in): a
+// single-element access to a state buffer must hit a node of the lattice
+// (population < K, row < ny, column < nx), a bulk row copy must stay inside
+// the buffer's slot of the allocation. A failing check skips the access and
+// sets ERR_BOUNDS; nothing traps. Without the flag the checks compile away.
+#ifdef LBM_BOUNDS_CHECK
+__device__ __forceinline__ bool bc_report(const LatDesc* d) {
+    atomicOr(d->err, ERR_BOUNDS);
+    return false;
+}
+__device__ __forceinline__ bool bc_node(const LatDesc* d, int K, long long off) {
+    bool ok = off >= 0 && off < (long long)K * d->plane;
+    if (ok) {
+        const long long r = off % d->plane;
+        ok = (r % d->pitch) < d->nx && (r / d->pitch) < d->ny;
+    }
+    return ok || bc_report(d);
+}
+__device__ __forceinline__ bool bc_span(const LatDesc* d, int K, long long off, long long n) {
+    return (off >= -STATE_HEAD && off + n <= (long long)K * d->plane + STATE_TAIL) || bc_report(d);
+}
+#define LBM_BC_NODE(d, K, off) bc_node((d), (K), (off))
+#define LBM_BC_SPAN(d, K, off, n) bc_span((d), (K), (off), (n))
+#else
+#define LBM_BC_NODE(d, K, off) true
+#define LBM_BC_SPAN(d, K, off, n) true
+#endif
 
 // A per-lattice constant in the kernel's precision.
 template <typename T>

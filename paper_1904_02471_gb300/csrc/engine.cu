@@ -41,6 +41,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 static const double SQRT3 = 1.73205080756887729353;
+static_assert(Lattice::HEAD == STATE_HEAD && Lattice::TAIL == STATE_TAIL, "state buffer layout");
 
 static double vmax_of(int q1) {
     switch (q1) {
@@ -190,7 +191,9 @@ int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
         L.mem = nullptr;
         return cuda_fail(e, "cudaMalloc(state)");
     }
-    e = cudaMemsetAsync(L.mem, 0, bytes, stream_);
+    // poison: every byte 0xFF, a NaN in float and double, so row padding and
+    // slack never read into a result without showing up as non-finite
+    e = cudaMemsetAsync(L.mem, 0xFF, bytes, stream_);
     if (e == cudaSuccess) e = cudaMalloc(&L.d_part, sizeof(double) * NOBS * 1024);
     if (e == cudaSuccess) e = cudaMalloc(&L.d_snap, sizeof(double) * NOBS);
     if (e != cudaSuccess) {
@@ -286,6 +289,7 @@ LatDesc Engine::make_desc(const Lattice& L, const Group& g, int item_begin, doub
     d.dt_tau_f = (float)L.dt_tau;
     d.rho0_f = (float)L.rho0s;
     d.eps_f = (float)L.eps;
+    d.err = g.d_hdr + 2;
     d.dt = L.spec.dt;
     d.probe_comp = L.probe_comp;
     d.obs_cap = (int)std::min<long long>(L.obs_cap, std::numeric_limits<int>::max());
@@ -594,6 +598,10 @@ int Engine::check_device_errors() {
             const int zero = 0;
             CK(cudaMemcpy(g.d_hdr + 2, &zero, sizeof zero, cudaMemcpyHostToDevice));
         }
+    }
+    if (bad & ERR_BOUNDS) {
+        set_error("a kernel reached outside a state buffer (caught by the bounds-checked build)");
+        return LBM_ECUDA;
     }
     if (bad) {
         set_error("a device-side wait ran out of time (bulk-copy pipeline); results of that step are invalid");

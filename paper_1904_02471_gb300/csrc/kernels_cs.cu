@@ -58,13 +58,15 @@ __device__ __forceinline__ void cs_plain_aa_rows(const LatDesc* dp, T* buf, int 
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+            long long off;
             if (MODE == CS_AA_EVEN) {
-                s[k] = buf[k * plane + row0 + x];
+                off = k * plane + row0 + x;
             } else {
                 const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
                 const long long sr = cy == 1 ? rowm : (cy == -1 ? rowp : row0);
-                s[k] = buf[(8 - k) * plane + sr + sx];
+                off = (8 - k) * plane + sr + sx;
             }
+            s[k] = LBM_BC_NODE(dp, 9, off) ? buf[off] : T(0);
         }
         T dr = T(0), jx = T(0), jy = T(0);
 #pragma unroll
@@ -83,13 +85,15 @@ __device__ __forceinline__ void cs_plain_aa_rows(const LatDesc* dp, T* buf, int 
             const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
             const T v = s[k] - omega * (s[k] - geq);
             const int cx = c3_of(k % 3), cy = c3_of(k / 3);
+            long long off;
             if (MODE == CS_AA_EVEN) {
-                buf[(8 - k) * plane + row0 + x] = v;
+                off = (8 - k) * plane + row0 + x;
             } else {
                 const int dxx = cx == 1 ? xp : (cx == -1 ? xm : x);
                 const long long drw = cy == 1 ? rowp : (cy == -1 ? rowm : row0);
-                buf[k * plane + drw + dxx] = v;
+                off = k * plane + drw + dxx;
             }
+            if (LBM_BC_NODE(dp, 9, off)) buf[off] = v;
         }
         if (obs) {
             acc[0] += dr;
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
                     const int cx = c3_of(k % 3), cy = c3_of(k / 3);
                     const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
                     const long long sr = cy == 1 ? rowm : (cy == -1 ? rowp : row0);
-                    s[k] = in[k * plane + sr + sx];
+                    s[k] = LBM_BC_NODE(dp, 9, k * plane + sr + sx) ? in[k * plane + sr + sx] : T(0);
                 }
                 // moments, Eq. (f_moments_discrete), ascending k
                 T dr = T(0), jx = T(0), jy = T(0);
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
                 for (int k = 0; k < 9; ++k) {
                     const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
                     const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
-                    out[k * plane + row0 + x] = s[k] - omega * (s[k] - geq);
+                    if (LBM_BC_NODE(dp, 9, k * plane + row0 + x)) out[k * plane + row0 + x] = s[k] - omega * (s[k] - geq);
                 }
                 if (obs) {
                     acc[0] += dr;
@@ -222,9 +226,9 @@ __host__ __device__ constexpr size_t cs_bulk_smem() {
 // buffers, plane k at row y - c_ky; in place, even step: plane k at row y;
 // odd step: plane 8 - k at row y - c_ky. Returns false when a wait ran out.
 template <typename T, int W, int S, int MODE>
-__device__ __forceinline__ bool cs_bulk_issue(T* ring, uint64_t* full, uint64_t* empty, const T* in, long long plane,
-                                              int pitch, int ny, int x0, int y0, int y1, unsigned& it, bool skip_first,
-                                              unsigned long long lim) {
+__device__ __forceinline__ bool cs_bulk_issue(const LatDesc* dp, T* ring, uint64_t* full, uint64_t* empty, const T* in,
+                                              long long plane, int pitch, int ny, int x0, int y0, int y1, unsigned& it,
+                                              bool skip_first, unsigned long long lim) {
     constexpr int SEG = W + 8;
     constexpr unsigned SEG_BYTES = SEG * sizeof(T);
     constexpr unsigned SLOT_BYTES = 9 * SEG_BYTES;
@@ -232,9 +236,23 @@ __device__ __forceinline__ bool cs_bulk_issue(T* ring, uint64_t* full, uint64_t*
         const int s = it % S;
         if (it >= (unsigned)S && !mbar_wait(&empty[s], ((it / S) - 1) & 1, lim)) return false;
         if (skip_first && it == 0) continue;   // injected: this slot is never filled
-        mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
         const int ym = (y == 0) ? ny - 1 : y - 1;
         const int yp = (y + 1 >= ny) ? y + 1 - ny : y + 1;
+#ifdef LBM_BOUNDS_CHECK
+        bool spans_ok = true;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int cy = c3_of(k / 3);
+            const int sy = MODE == CS_AA_EVEN ? y : (cy == 1 ? ym : (cy == -1 ? yp : y));
+            const int sp = MODE == CS_AA_ODD ? 8 - k : k;
+            spans_ok = spans_ok && LBM_BC_SPAN(dp, 9, sp * plane + (long long)sy * pitch + x0 - 4, SEG);
+        }
+        if (!spans_ok) {   // no copy: the slot completes empty (the step is reported invalid)
+            mbar_arrive(&full[s]);
+            continue;
+        }
+#endif
+        mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int cy = c3_of(k / 3);
@@ -287,7 +305,8 @@ __device__ __forceinline__ void cs_bulk_consume(const T* ring, uint64_t* full, u
                     if ((cx == 1 && x == 0) || (cx == -1 && x == nx - 1)) {
                         const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
                         const int sp = MODE == CS_AA_ODD ? 8 - k : k;
-                        f[k] = in[sp * plane + (long long)sy * pitch + (cx == 1 ? nx - 1 : 0)];
+                        const long long off = sp * plane + (long long)sy * pitch + (cx == 1 ? nx - 1 : 0);
+                        f[k] = LBM_BC_NODE(dp, 9, off) ? in[off] : T(0);
                     }
                 }
             }
@@ -308,16 +327,18 @@ __device__ __forceinline__ void cs_bulk_consume(const T* ring, uint64_t* full, u
                 const T xi = (T)vx_of<3>(k) * ux + (T)vy_of<3>(k) * uy;
                 const T geq = (T)w_of<3>(k) * (dr + rho * (xi + T(0.5) * (xi * xi - usq)));
                 const T v = f[k] - omega * (f[k] - geq);
+                long long off;
                 if (MODE == CS_AB) {
-                    __stcs(out + k * plane + row0, v);
+                    off = k * plane + row0;
                 } else if (MODE == CS_AA_EVEN) {
-                    __stcs(out + (8 - k) * plane + row0, v);
+                    off = (8 - k) * plane + row0;
                 } else {
                     const int cx = c3_of(k % 3), cy = c3_of(k / 3);
                     const int dxx = cx == 1 ? (x + 1 >= nx ? 0 : x + 1) : (cx == -1 ? (x == 0 ? nx - 1 : x - 1) : x);
                     const int dyy = cy == 1 ? yp : (cy == -1 ? ym : y);
-                    __stcs(out + k * plane + (long long)dyy * pitch + dxx, v);
+                    off = k * plane + (long long)dyy * pitch + dxx;
                 }
+                if (LBM_BC_NODE(dp, 9, off)) __stcs(out + off, v);
             }
             if (obs) {
                 acc[0] += dr;
@@ -387,12 +408,12 @@ __global__ void __launch_bounds__(32 + W, cs_bulk_min_blocks<T, W>()) cs_bulk_ke
             const int mode = cs_mode(*dp, j);
             const T* in = static_cast<const T*>(dp->buf[mode == CS_AB ? dp->cur ^ (j & 1) : 0]);
             if (mode == CS_AB)
-                ok = cs_bulk_issue<T, W, S, CS_AB>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it, skip_first, lim);
+                ok = cs_bulk_issue<T, W, S, CS_AB>(dp, ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it, skip_first, lim);
             else if (mode == CS_AA_EVEN)
-                ok = cs_bulk_issue<T, W, S, CS_AA_EVEN>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
+                ok = cs_bulk_issue<T, W, S, CS_AA_EVEN>(dp, ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
                                                         skip_first, lim);
             else
-                ok = cs_bulk_issue<T, W, S, CS_AA_ODD>(ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
+                ok = cs_bulk_issue<T, W, S, CS_AA_ODD>(dp, ring, full, empty, in, plane, pitch, ny, x0, y0, y1, it,
                                                        skip_first, lim);
         }
         if (!ok) atomicOr(g.hdr + 2, ERR_WAIT_TIMEOUT);

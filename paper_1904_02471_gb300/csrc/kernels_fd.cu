@@ -220,7 +220,9 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             for (int i = tid; i < K * HY * RV; i += NT) {
                 const int k = i / (HY * RV), rem = i - k * (HY * RV);
                 const int r = rem / RV, c = rem - r * RV;
-                cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, src + k * plane + (long long)r * pitch + c * VEC);
+                [[maybe_unused]] const long long off = k * plane + (long long)(y0 - 3 + r) * pitch + (x0 - 4 + c * VEC);
+                if (LBM_BC_NODE(dp, K, off) && LBM_BC_NODE(dp, K, off + VEC - 1))
+                    cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, src + k * plane + (long long)r * pitch + c * VEC);
             }
             cp_async_wait_all();
         } else {
@@ -234,7 +236,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             for (int i = tid; i < K * HXY; i += NT) {
                 const int k = i / HXY, rem = i - k * HXY;
                 const int r = rem / HXP, c = rem - r * HXP;
-                cp_async_small<sizeof(T)>(tiles + i, U + k * plane + s_row[r] + s_col[c]);
+                if (LBM_BC_NODE(dp, K, k * plane + s_row[r] + s_col[c]))
+                    cp_async_small<sizeof(T)>(tiles + i, U + k * plane + s_row[r] + s_col[c]);
             }
             cp_async_wait_all();
         }
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
                     fy[TY * TX + tx] = f.y;
                 }
-                fnv[p] = (stage != 1 && active) ? fnp[k * plane] : T(0);
+                fnv[p] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
             }
             __syncthreads();
             if (active) {
@@ -378,7 +381,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     const T inc = (geq - uk) * dtt - a * cdx;
                     // stage combination in increment form: one rounding of the
                     // stored value per stage (u - f^n is exact for close values)
-                    op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
+                    if (LBM_BC_NODE(dp, K, cell + k * plane))
+                        op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
                 }
             }
         }

@@ -59,7 +59,8 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
                 xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
                 yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
             }
-            out[(m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd] = (T)dev;
+            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd;
+            if (LBM_BC_NODE(d, K, off)) out[off] = (T)dev;
         }
     }
 }
@@ -84,7 +85,8 @@ __global__ void set_pop_kernel(const LatDesc* d, int nx, int ny, const double* _
                 xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
                 yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
             }
-            out[(m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd] = (T)(f[k * n + c] - w_of<Q1>(k) * r0);
+            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd;
+            if (LBM_BC_NODE(d, K, off)) out[off] = (T)(f[k * n + c] - w_of<Q1>(k) * r0);
         }
     }
 }
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
                 xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
                 ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             }
-            const double s = (double)in[(m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs];
+            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs;
+            const double s = LBM_BC_NODE(d, K, off) ? (double)in[off] : 0.0;
             if (f) f[k * n + c] = s + w_of<Q1>(k) * r0;
             dr += s;
             jx += s * vx_of<Q1>(k);

@@ -16,7 +16,9 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
+# LBM_LIBRARY selects another build of the same library (e.g. the
+# bounds-checked one in _build_bounds/)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ECFL, LBM_ESTIFF, LBM_ENOMEM, LBM_ECUDA = 0, 1, 2, 3, 4, 5
 LBM_ENOTREADY, LBM_ETIMEOUT, LBM_EBUSY, LBM_ENONFINITE, LBM_ECANCELLED, LBM_ENOTFOUND = 6, 7, 8, 9, 10, 11
