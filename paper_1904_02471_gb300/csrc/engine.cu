@@ -10,6 +10,8 @@
 // descriptors and probe tables are small side allocations.
 #include "engine.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -41,6 +43,15 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 static const double SQRT3 = 1.73205080756887729353;
+
+// NVTX range for the lifetime of the object (tools such as Nsight Compute
+// filter launches by range; without a tool attached the calls do nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 static_assert(Lattice::HEAD == STATE_HEAD && Lattice::TAIL == STATE_TAIL, "state buffer layout");
 
 static double vmax_of(int q1) {
@@ -458,8 +469,10 @@ void Engine::mirror_advance(int c) {
 
 int Engine::step(long long n) {
     if (n < 0) { set_error("negative step count"); return LBM_EINVAL; }
+    NvtxRange range("lbm.step");
     while (n > 0) {
         const int c = (int)std::min<long long>(n, chunk);
+        NvtxRange chunk_range(use_graphs && c == chunk && chunk > 1 ? "lbm.chunk.graph" : "lbm.chunk");
         if (use_graphs && c == chunk && chunk > 1) {
             if (!graph_ || graph_chunk_ != c) {
                 invalidate_graph();
@@ -500,6 +513,7 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
     for (int i = 0; i < cap; ++i) ms[i] = 0.0;
     if (total_ms) *total_ms = 0.0;
     if (n == 0) return LBM_OK;
+    NvtxRange range("lbm.step_profiled");
     // events: per step and group, one before and one after each launch
     struct Mark { int slot; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -521,6 +535,8 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
             const GroupDev gd = g.dev();
             const int nk = g.model == LBM_CS ? 1 : 3;
             for (int st = 1; st <= nk; ++st) {
+                static const char* const kNames[4] = {"lbm.cs_step", "lbm.fd_stage1", "lbm.fd_stage2", "lbm.fd_stage3"};
+                NvtxRange kernel_range(kNames[g.model == LBM_CS ? 0 : st]);
                 cudaEvent_t a = ev(), b = ev();
                 if (!a || !b) { cleanup(); return cuda_fail(cudaGetLastError(), "cudaEventCreate"); }
                 cudaEventRecord(a, stream_);
