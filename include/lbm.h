@@ -174,14 +174,16 @@ int lbm_get_spec(const lbm_ctx* ctx, lbm_spec* out);
 int lbm_set_weno_eps(lbm_ctx* ctx, double eps);
 
 /* Initialise f = f^eq(rho, u) (Eq. herfeq) from host fields rho, ux, uy,
- * each [ny][nx]; rho must be > 0 and finite (LBM_EINVAL otherwise). The step
+ * each [ny][nx]; rho must be > 0 and finite and u finite, else LBM_EINVAL
+ * (checked on the device; the state is then not initialised). The step
  * counter restarts at 0. The paper does not state its initial populations;
  * the equilibrium is the reading used here. */
 int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 
 /* Load an arbitrary state: f is [K][ny][nx] full populations (for
- * LBM_FP32_DEV they are stored as float32(f - w_k rho0)). The step counter
- * is kept. */
+ * LBM_FP32_DEV they are stored as float32(f - w_k rho0)); a non-finite value
+ * gives LBM_EINVAL (checked on the device; the state is then not set). The
+ * step counter is kept. */
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
 
 /* Enqueue n >= 0 time steps on the context stream and return. One step is

@@ -61,9 +61,11 @@ struct LatDesc {
 // elements (row segments of bulk copies may reach into them).
 constexpr long long STATE_HEAD = 4, STATE_TAIL = 1024;
 
-// Error bit of the group error word: an access outside a state buffer caught
-// by the bounds-checked build.
+// Error bits of the group error word: an access outside a state buffer caught
+// by the bounds-checked build; an input value rejected by the state
+// initialisation kernels (rho <= 0 or a non-finite value).
 constexpr int ERR_BOUNDS = 2;
+constexpr int ERR_INPUT = 4;
 
 // Bounds-checked build (-DLBM_BOUNDS_CHECK; compute-sanitizer stand-in): a
 // single-element access to a state buffer must hit a node of the lattice

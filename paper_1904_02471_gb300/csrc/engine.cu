@@ -644,13 +644,22 @@ static bool all_finite(const double* a, size_t n) {
     return true;
 }
 
+// Input errors the state initialisation kernels flagged in the group's error
+// word (the values are checked on the device, where they are read anyway):
+// cleared here; true if there were any.
+bool Engine::take_input_error(const Group& g) {
+    int h = 0;
+    if (cudaMemcpy(&h, g.d_hdr + 2, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    if (!(h & ERR_INPUT)) return false;
+    h &= ~ERR_INPUT;
+    cudaMemcpy(g.d_hdr + 2, &h, sizeof h, cudaMemcpyHostToDevice);
+    return true;
+}
+
 int Engine::init(int i, const double* rho, const double* ux, const double* uy) {
     if (!valid(i) || !rho || !ux || !uy) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     const size_t n = (size_t)L.spec.nx * L.spec.ny;
-    for (size_t c = 0; c < n; ++c)
-        if (!(rho[c] > 0) || !std::isfinite(rho[c])) { set_error("rho must be positive and finite"); return LBM_EINVAL; }
-    if (!all_finite(ux, n) || !all_finite(uy, n)) { set_error("u must be finite"); return LBM_EINVAL; }
     int rc = ensure_io(L, sizeof(double) * 3 * n);
     if (rc) return rc;
     L.step0 = 0;
@@ -666,6 +675,10 @@ int Engine::init(int i, const double* rho, const double* ux, const double* uy) {
     CK(launch_init_equilibrium(L.spec.precision, L.spec.q_per_axis, L.spec.model == LBM_CS, g.d_desc + L.slot,
                                L.spec.nx, L.spec.ny, L.d_io, L.d_io + n, L.d_io + 2 * n, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (take_input_error(g)) {
+        set_error("rho must be positive and finite and u finite (the state is not initialised)");
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 
@@ -673,7 +686,6 @@ int Engine::set_populations(int i, const double* f) {
     if (!valid(i) || !f) { set_error("bad arguments"); return LBM_EINVAL; }
     Lattice& L = lat[i];
     const size_t n = (size_t)L.spec.nx * L.spec.ny * L.K;
-    if (!all_finite(f, n)) { set_error("populations must be finite"); return LBM_EINVAL; }
     int rc = ensure_io(L, sizeof(double) * n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(L.d_io, f, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
@@ -681,6 +693,10 @@ int Engine::set_populations(int i, const double* f) {
     CK(launch_set_populations(L.spec.precision, L.spec.q_per_axis, L.spec.model == LBM_CS, g.d_desc + L.slot,
                               L.spec.nx, L.spec.ny, L.d_io, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (take_input_error(g)) {
+        set_error("populations must be finite (the state is not set)");
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 

@@ -119,6 +119,7 @@ class Engine {
     long long kernel_launches() const { return launches_; }
     int sync();
     int check_device_errors();
+    bool take_input_error(const Group& g);
     // Test injection of a device-side wait that runs out (see lbm.h,
     // lbm_inject_wait_timeout): 0 = off, else the wait limit in microseconds.
     int inject_wait_timeout(int microseconds);

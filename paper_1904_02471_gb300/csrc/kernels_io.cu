@@ -45,13 +45,18 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
-        const double r = rho[c], u = ux[c], v = uy[c];
-        const double usq = u * u + v * v;
+        const double rd = rho[c], ud = ux[c], vd = uy[c];
+        // input check on the device (every value is read here anyway)
+        if (!(rd > 0.0) || !isfinite(rd) || !isfinite(ud) || !isfinite(vd)) atomicOr(d->err, ERR_INPUT);
+        // arithmetic in the storage precision: float for the deviation
+        // storage, whose rho - rho0 is formed in double first
+        const T dr = (T)(rd - r0), r = (T)rd, u = (T)ud, v = (T)vd;
+        const T usq = u * u + v * v;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const double xi = vx_of<Q1>(k) * u + vy_of<Q1>(k) * v;
+            const T xi = (T)vx_of<Q1>(k) * u + (T)vy_of<Q1>(k) * v;
             // Eq. (herfeq) minus the storage offset w_k rho0
-            const double dev = w_of<Q1>(k) * ((r - r0) + r * (xi + 0.5 * (xi * xi - usq)));
+            const T dev = (T)w_of<Q1>(k) * (dr + r * (xi + T(0.5) * (xi * xi - usq)));
             int xd = x, yd = y;
             if (m.shift) {
                 xd = x - lat_c<Q1>(k % Q1);
@@ -86,7 +91,9 @@ __global__ void set_pop_kernel(const LatDesc* d, int nx, int ny, const double* _
                 yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
             }
             const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd;
-            if (LBM_BC_NODE(d, K, off)) out[off] = (T)(f[k * n + c] - w_of<Q1>(k) * r0);
+            const double fv = f[k * n + c];
+            if (!isfinite(fv)) atomicOr(d->err, ERR_INPUT);
+            if (LBM_BC_NODE(d, K, off)) out[off] = (T)(fv - w_of<Q1>(k) * r0);
         }
     }
 }
@@ -142,6 +149,48 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
         if (pc >= 0) acc[3] += (pc == 0 ? u : v) * d->probe_px[x] * d->probe_py[y];
     }
     if (part) block_reduce_obs<double, IO_THREADS>(acc, part + (long long)blockIdx.x * NOBS, red);
+}
+
+// Observables of the whole lattice (no readout): per node the moments in the
+// storage precision and, for the probed component only, the velocity; from
+// there on float64 (per-thread sums, block reduction, two-level finalise).
+template <typename T, int Q1, bool PULL>
+__global__ void __launch_bounds__(IO_THREADS) obs_snapshot_kernel(const LatDesc* d, int nx, int ny,
+                                                                  double* __restrict__ part) {
+    constexpr int K = Q1 * Q1;
+    __shared__ double red[(IO_THREADS / 32) * NOBS];
+    const long long plane = d->plane;
+    const int pitch = d->pitch;
+    const T r0 = (T)d->rho0;
+    const StoreMap m = store_map<PULL>(d);
+    const T* __restrict__ in = static_cast<const T*>(d->buf[m.buf]);
+    const int pc = d->probe_comp;
+    const long long n = (long long)nx * ny;
+    double acc[NOBS] = {0.0, 0.0, 0.0, 0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            int xs = x, ys = y;
+            if (m.shift) {
+                xs = x - lat_c<Q1>(k % Q1);
+                ys = y - lat_c<Q1>(k / Q1);
+                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            }
+            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs;
+            const T s = LBM_BC_NODE(d, K, off) ? in[off] : T(0);
+            dr += s;
+            if (vx_of<Q1>(k) != 0.0) jx += s * (T)vx_of<Q1>(k);
+            if (vy_of<Q1>(k) != 0.0) jy += s * (T)vy_of<Q1>(k);
+        }
+        acc[0] += (double)dr;
+        acc[1] += (double)jx;
+        acc[2] += (double)jy;
+        if (pc >= 0) acc[3] += (double)((pc == 0 ? jx : jy) / (r0 + dr)) * d->probe_px[x] * d->probe_py[y];
+    }
+    block_reduce_obs<double, IO_THREADS>(acc, part + (long long)blockIdx.x * NOBS, red);
 }
 
 // Deterministic block sum of n rows of NOBS doubles.
@@ -271,8 +320,12 @@ cudaError_t launch_readout(int precision, int q1, int pull, const LatDesc* d, in
                            cudaStream_t s) {
     int grid = io_grid((long long)wx * wy);
     if (part && grid > nblocks) grid = nblocks;
-    LBM_DISPATCH_Q(q1, pull, precision,
-                   (readout_kernel<T, Q, P><<<grid, IO_THREADS, 0, s>>>(d, nx, ny, x0, y0, wx, wy, f, rho, ux, uy, part)));
+    if (part && !f && !rho && x0 == 0 && y0 == 0 && wx == nx && wy == ny)
+        LBM_DISPATCH_Q(q1, pull, precision, (obs_snapshot_kernel<T, Q, P><<<grid, IO_THREADS, 0, s>>>(d, nx, ny, part)));
+    else
+        LBM_DISPATCH_Q(q1, pull, precision,
+                       (readout_kernel<T, Q, P><<<grid, IO_THREADS, 0, s>>>(d, nx, ny, x0, y0, wx, wy, f, rho, ux, uy,
+                                                                              part)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !part) return e;
     snap_finalize_kernel<<<1, FIN_THREADS, 0, s>>>(const_cast<LatDesc*>(d), part, grid);

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_partials_kernel(Noall
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % a.nx), y = (int)(c / a.nx);
-        double dr = 0.0, jx = 0.0, jy = 0.0;
+        // per node in the storage precision, then float64 (as lbm_observables)
+        T dr = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int xs = x, ys = y;
@@ -64,18 +65,15 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_partials_kernel(Noall
                 xs = xs < 0 ? xs + a.nx : (xs >= a.nx ? xs - a.nx : xs);
                 ys = ys < 0 ? ys + a.ny : (ys >= a.ny ? ys - a.ny : ys);
             }
-            const double s = (double)in[k * a.plane + (long long)ys * a.pitch + xs];
+            const T s = in[k * a.plane + (long long)ys * a.pitch + xs];
             dr += s;
-            jx += s * vx_of<Q1>(k);
-            jy += s * vy_of<Q1>(k);
+            if (vx_of<Q1>(k) != 0.0) jx += s * (T)vx_of<Q1>(k);
+            if (vy_of<Q1>(k) != 0.0) jy += s * (T)vy_of<Q1>(k);
         }
-        acc[0] += dr;
-        acc[1] += jx;
-        acc[2] += jy;
-        if (a.comp >= 0) {
-            const double r = a.rho0 + dr;
-            acc[3] += (a.comp == 0 ? jx / r : jy / r) * a.px[x] * a.py[y];
-        }
+        acc[0] += (double)dr;
+        acc[1] += (double)jx;
+        acc[2] += (double)jy;
+        if (a.comp >= 0) acc[3] += (double)((a.comp == 0 ? jx : jy) / ((T)a.rho0 + dr)) * a.px[x] * a.py[y];
     }
     block_reduce_obs<double, NOALLOC_THREADS>(acc, part + (long long)blockIdx.x * NOBS, red);
 }

@@ -359,3 +359,46 @@ def test_fd_every_tile_variant(prec, q, nx, ny):
         assert np.array_equal(f, res[0][1]), cfg
     if prec == "fp64":
         assert rel_err(res[0][1], oracle.fd_run(f0, dx, dt, tau, 12)) < TOL64
+
+
+@pytest.mark.parametrize("model,q", [("cs", 3), ("fd", 4)])
+@pytest.mark.parametrize("bad", ["rho_zero", "rho_negative", "ux_nan", "uy_inf", "rho_nan"])
+def test_init_rejects_bad_fields_on_the_device(model, q, bad):
+    """Input checks run in the initialisation kernel: one bad node anywhere
+    gives LBM_EINVAL, and the lattice can be initialised again afterwards."""
+    from paper_1904_02471_gb300 import lbm
+    nx, ny = 37, 11
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=71)
+    name, kind = bad.split("_")
+    args = {"rho": rho, "ux": ux, "uy": uy}
+    field = args[name].copy()
+    field[7, 29] = {"zero": 0.0, "negative": -0.5, "nan": np.nan, "inf": np.inf}[kind]
+    args[name] = field
+    kw = dict(dt=1e-3) if model == "fd" else {}
+    tau = 0.6 if model == "cs" else 2e-3
+    with pkg.Lattice(model, q, nx, ny, tau, **kw) as L:
+        with pytest.raises(lbm.LbmError) as err:
+            L.init(args["rho"], args["ux"], args["uy"])
+        assert err.value.code == lbm.LBM_EINVAL
+        L.init(rho, ux, uy)
+        L.step(3)
+        f = L.populations()
+    f0 = oracle.equilibrium(q, rho, ux, uy)
+    ref = oracle.cs_run(f0, tau, 3) if model == "cs" else oracle.fd_run(f0, 1.0 / nx, 1e-3, tau, 3)
+    assert rel_err(f, ref) < TOL64
+
+
+def test_set_populations_rejects_non_finite_values():
+    from paper_1904_02471_gb300 import lbm
+    nx, ny = 20, 13
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=72)
+    f0 = oracle.equilibrium(3, rho, ux, uy)
+    bad = f0.copy()
+    bad[4, 12, 19] = np.nan
+    with pkg.Lattice("cs", 3, nx, ny, 0.6, storage="inplace") as L:
+        with pytest.raises(lbm.LbmError) as err:
+            L.set_populations(bad)
+        assert err.value.code == lbm.LBM_EINVAL
+        L.set_populations(f0)
+        L.step(2)
+        assert rel_err(L.populations(), oracle.cs_run(f0, 0.6, 2)) < TOL64
