@@ -227,17 +227,33 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             cp_async_wait_all();
         } else {
             // periodic edge: wrapped row offsets and columns once per tile,
-            // then one asynchronous element copy per staged value
+            // then asynchronous copies from the wrapped positions
             for (int i = tid; i < HY + HXP; i += NT) {
                 if (i < HY) s_row[i] = (long long)wrapi(y0 - 3 + i, ny) * pitch;
                 else s_col[i - HY] = wrapi(x0 - 4 + (i - HY), nx);
             }
             __syncthreads();
-            for (int i = tid; i < K * HXY; i += NT) {
-                const int k = i / HXY, rem = i - k * HXY;
-                const int r = rem / HXP, c = rem - r * HXP;
-                if (LBM_BC_NODE(dp, K, k * plane + s_row[r] + s_col[c]))
-                    cp_async_small<sizeof(T)>(tiles + i, U + k * plane + s_row[r] + s_col[c]);
+            constexpr int VEC = 16 / sizeof(T);
+            if (nx % VEC == 0) {
+                // a 16-byte column chunk starts at a multiple of VEC and the
+                // wrap point nx is one, so no chunk straddles it: one copy
+                // per chunk from its wrapped start column
+                constexpr int RV = HXP / VEC;
+#pragma unroll 4
+                for (int i = tid; i < K * HY * RV; i += NT) {
+                    const int k = i / (HY * RV), rem = i - k * (HY * RV);
+                    const int r = rem / RV, c = rem - r * RV;
+                    const long long off = k * plane + s_row[r] + s_col[c * VEC];
+                    if (LBM_BC_NODE(dp, K, off) && LBM_BC_NODE(dp, K, off + VEC - 1))
+                        cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, U + off);
+                }
+            } else {
+                for (int i = tid; i < K * HXY; i += NT) {
+                    const int k = i / HXY, rem = i - k * HXY;
+                    const int r = rem / HXP, c = rem - r * HXP;
+                    if (LBM_BC_NODE(dp, K, k * plane + s_row[r] + s_col[c]))
+                        cp_async_small<sizeof(T)>(tiles + i, U + k * plane + s_row[r] + s_col[c]);
+                }
             }
             cp_async_wait_all();
         }
