@@ -424,14 +424,17 @@ def _lat_kwargs(pkg, d, prec):
                 precision=prec)
 
 
-def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=(1000, 5000), duration_s=30.0):
+def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=(1000, 5000), duration_s=30.0,
+               rate_per_s=None, budget_gb=64):
     """Served stream: Poisson arrivals of CS / FD Taylor-Green runs (FP32)
-    into the continuous-batching server; latency = completion - arrival."""
+    into the continuous-batching server; latency = completion - arrival.
+    The arrival rate is n_req / duration_s unless rate_per_s is given."""
     import paper_1904_02471_gb300 as pkg
     from paper_1904_02471_gb300 import lbm
-    reqs = wl.served_stream(n_req, seed, rate_per_s=n_req / duration_s, sides=sides, steps=steps)
+    rate = rate_per_s if rate_per_s else n_req / duration_s
+    reqs = wl.served_stream(n_req, seed, rate_per_s=rate, sides=sides, steps=steps)
     work = sum(r["n"] ** 2 * r["steps"] for r in reqs)
-    S = lbm.Server(64 << 30, 256, 128)
+    S = lbm.Server(budget_gb << 30, 256, 128)
     t0 = time.perf_counter()
     tickets = []
     for r in reqs:
@@ -441,14 +444,15 @@ def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=
         spec = _instance_spec(pkg, {"model": r["model"], "n": r["n"], "tau_star": r["tau_star"]}, "fp32")
         U = U0 * (math.sqrt(3.0) if r["model"] == "cs" else 1.0)
         tickets.append(S.submit(lbm.make_request(spec, r["steps"], "tg", U, obs_every=0)))
-    S.drain(1800)
+    S.drain(7200)
     res = [S.poll(t) for t in tickets]
     S.close()
     lat = sorted(x["t_done"] - x["t_submit"] for x in res)
     makespan = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
     ok = sum(1 for x in res if x["status"] == 0)
+    span = reqs[-1]["arrival"]
     return {
-        "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{duration_s:.0f} s, CS or FD 16-velocity "
+        "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{span:.0f} s, CS or FD 16-velocity "
                     f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2), steps U[{steps[0]},{steps[1]}], FP32 "
                     "(CS in place)",
         "requests": n_req, "completed_ok": ok,
@@ -457,6 +461,53 @@ def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=
                       "max": round(lat[-1], 4)},
         "makespan_s": round(makespan, 3),
     }
+
+
+def lattice_rates(torch, sides, steps=8):
+    """Single-lattice FP32 rates (lattice updates per second) of the served
+    instance kinds, CS (in place) and FD 16-velocity, per side: a few steps
+    of one lattice alone after one untimed step."""
+    import paper_1904_02471_gb300 as pkg
+    rates = {}
+    for model in ("cs", "fd"):
+        for n in sides:
+            d = {"model": model, "n": n, "tau_star": 0.8}
+            s = _instance_spec(pkg, d, "fp32")
+            with pkg.Lattice(model, s.q_per_axis, n, n, s.tau, dt=s.dt, precision="fp32",
+                             storage="inplace" if model == "cs" else "ab") as L:
+                L.init(*_fields(d))
+                L.step(1)
+                L.sync()
+                k = steps if model == "fd" and n > 512 else 64 * steps
+                t0 = time.perf_counter()
+                L.step(k)
+                L.sync()
+                rates[(model, n)] = n * n * k / (time.perf_counter() - t0)
+    return rates
+
+
+def run_served_full(torch, n_req, loads, seed=0):
+    """The served-stream configuration in full: sides 64^2..4096^2, 1k..20k
+    steps. The arrival rate is set to `load` times an estimate of the
+    capacity: the mean service time of a request of the stream, each lattice
+    run alone at its measured single-lattice rate (an underestimate of the
+    server's capacity, which batches small lattices)."""
+    sides = (64, 128, 256, 512, 1024, 2048, 4096)
+    steps = (1000, 20000)
+    rates = lattice_rates(torch, sides)
+    probe = wl.served_stream(n_req, seed, rate_per_s=1.0, sides=sides, steps=steps)
+    service = sum(r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in probe) / n_req
+    out = {"metric": "served stream, full configuration", "unit": "MLUPS", "dtype": "f32",
+           "data": "synthetic (Taylor-Green initial states, seeded arrivals)",
+           "single_lattice_mlups": {f"{m}{n}": round(v / 1e6, 1) for (m, n), v in rates.items()},
+           "mean_service_s_alone": round(service, 3), "runs": []}
+    for load in loads:
+        rec = run_served(torch, n_req=n_req, seed=seed, sides=sides, steps=steps, rate_per_s=load / service,
+                         budget_gb=128)
+        rec["load"] = load
+        rec["rate_per_s"] = round(load / service, 5)
+        out["runs"].append(rec)
+    return out
 
 
 def fd_tile_height(report, gi):
@@ -522,7 +573,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
+    ap.add_argument("--served-full", type=int, default=0, metavar="N_REQ",
+                    help="only run the served stream in its full configuration (sides up to 4096^2, up to 20k "
+                         "steps) with N_REQ requests, at each --served-load, and print that record")
+    ap.add_argument("--served-load", type=float, nargs="+", default=[1.0, 1.5])
     args = ap.parse_args()
+    if args.served_full:
+        import torch
+        torch.cuda.init()
+        print(json.dumps(run_served_full(torch, args.served_full, args.served_load)))
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))
