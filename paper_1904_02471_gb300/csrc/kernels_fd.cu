@@ -156,6 +156,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     constexpr int NFX = (TX + 1) * TY;   // faces normal to x: [TY][TX + 1]
     constexpr int NFY = TX * (TY + 1);   // faces normal to y: [TY + 1][TX]
     constexpr int NF = NFX + NFY;
+    constexpr int VEC = 16 / sizeof(T);   // values per 16-byte copy
+    constexpr int RV = HXP / VEC;         // 16-byte chunks per staged row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = fd_group<T, Q1>();
     T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
@@ -205,6 +207,34 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         const V eps = P::sp(lat_val<T>(dp->eps, dp->eps_f) * T(12.0 / 13.0));
         const long long cell = (long long)y * pitch + x;
         const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+        // 16-byte asynchronous copies of the K halo tiles: a thread owns one
+        // (row, 16-byte column chunk) of the tile and copies it for every
+        // SK-th population, stepping by whole planes (no index arithmetic per
+        // copy); row_src(r, c) is the source of population 0
+        auto stage_rows16 = [&](int t, auto row_src) {
+            constexpr int PAIRS = HY * RV;
+            if constexpr (NT >= PAIRS) {
+                constexpr int SK = NT / PAIRS;
+                if (t < SK * PAIRS) {
+                    const int pr = t % PAIRS, k0 = t / PAIRS;
+                    const int r = pr / RV, c = pr - r * RV;
+                    const T* sp = row_src(r, c) + k0 * plane;
+                    T* dp16 = tiles + k0 * HXY + r * HXP + c * VEC;
+#pragma unroll 4
+                    for (int k = k0; k < K; k += SK, sp += SK * plane, dp16 += SK * HXY)
+                        if (LBM_BC_NODE(dp, K, sp - U) && LBM_BC_NODE(dp, K, sp - U + VEC - 1)) cp_async16(dp16, sp);
+                }
+            } else {
+                for (int pr = t; pr < PAIRS; pr += NT) {
+                    const int r = pr / RV, c = pr - r * RV;
+                    const T* sp = row_src(r, c);
+                    T* dp16 = tiles + r * HXP + c * VEC;
+#pragma unroll 4
+                    for (int k = 0; k < K; ++k, sp += plane, dp16 += HXY)
+                        if (LBM_BC_NODE(dp, K, sp - U) && LBM_BC_NODE(dp, K, sp - U + VEC - 1)) cp_async16(dp16, sp);
+                }
+            }
+        };
 
         // 1. stage all K halo tiles of the stage input
         __syncthreads();  // the previous item is done with the tiles (and s_obs)
@@ -213,17 +243,8 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             // rows are 16-byte aligned (x0 - 4 is a multiple of 4, pitch of
             // 32): every thread issues all its 16-byte asynchronous copies,
             // then waits once
-            constexpr int VEC = 16 / sizeof(T);
-            constexpr int RV = HXP / VEC;
             const T* src = U + (long long)(y0 - 3) * pitch + (x0 - 4);
-#pragma unroll 4
-            for (int i = tid; i < K * HY * RV; i += NT) {
-                const int k = i / (HY * RV), rem = i - k * (HY * RV);
-                const int r = rem / RV, c = rem - r * RV;
-                [[maybe_unused]] const long long off = k * plane + (long long)(y0 - 3 + r) * pitch + (x0 - 4 + c * VEC);
-                if (LBM_BC_NODE(dp, K, off) && LBM_BC_NODE(dp, K, off + VEC - 1))
-                    cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, src + k * plane + (long long)r * pitch + c * VEC);
-            }
+            stage_rows16(tid, [&](int r, int c) { return src + (long long)r * pitch + c * VEC; });
             cp_async_wait_all();
         } else {
             // periodic edge: wrapped row offsets and columns once per tile,
@@ -233,20 +254,11 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                 else s_col[i - HY] = wrapi(x0 - 4 + (i - HY), nx);
             }
             __syncthreads();
-            constexpr int VEC = 16 / sizeof(T);
             if (nx % VEC == 0) {
                 // a 16-byte column chunk starts at a multiple of VEC and the
                 // wrap point nx is one, so no chunk straddles it: one copy
                 // per chunk from its wrapped start column
-                constexpr int RV = HXP / VEC;
-#pragma unroll 4
-                for (int i = tid; i < K * HY * RV; i += NT) {
-                    const int k = i / (HY * RV), rem = i - k * (HY * RV);
-                    const int r = rem / RV, c = rem - r * RV;
-                    const long long off = k * plane + s_row[r] + s_col[c * VEC];
-                    if (LBM_BC_NODE(dp, K, off) && LBM_BC_NODE(dp, K, off + VEC - 1))
-                        cp_async16(tiles + (size_t)k * HXY + r * HXP + c * VEC, U + off);
-                }
+                stage_rows16(tid, [&](int r, int c) { return U + s_row[r] + s_col[c * VEC]; });
             } else {
                 for (int i = tid; i < K * HXY; i += NT) {
                     const int k = i / HXY, rem = i - k * HXY;
