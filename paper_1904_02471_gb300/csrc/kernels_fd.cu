@@ -126,15 +126,24 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 constexpr int FD_TX = 32;
 constexpr int FD_HXP = 40;
 
-// Populations whose faces are evaluated between two barriers: 4, or 2 where
-// four face groups would not fit next to the halo tiles (FP64, 25 velocities).
-template <typename T, int Q1>
-__host__ __device__ constexpr int fd_group() { return (sizeof(T) == 8 && Q1 == 5) ? 2 : 4; }
+// Populations whose faces are evaluated between two barriers (a group): 4,
+// or 2 where four face groups would not fit next to the halo tiles (FP64, 25
+// velocities), or 8 for FP32 32 x 8 tiles: warp p evaluates the edge faces of
+// the group's p-th population, so a group of as many populations as the tile
+// has warps gives every warp the same work between two barriers.
+template <typename T, int Q1, int TY>
+__host__ __device__ constexpr int fd_group() {
+    return (sizeof(T) == 8 && Q1 == 5) ? 2 : (sizeof(T) == 4 && TY == 8 ? 8 : 4);
+}
+// Face buffers: two alternate between groups (one barrier per group); a
+// group of 8 has one (two barriers per group, the same shared memory).
+template <typename T, int Q1, int TY>
+__host__ __device__ constexpr int fd_face_bufs() { return fd_group<T, Q1, TY>() == 8 ? 1 : 2; }
 
 template <typename T, int Q1, int TY>
 __host__ __device__ constexpr size_t fd_smem_bytes() {
     return sizeof(T) * ((size_t)Q1 * Q1 * (TY + 6) * FD_HXP +
-                        2 * fd_group<T, Q1>() * ((FD_TX + 1) * TY + FD_TX * (TY + 1))) +
+                        fd_face_bufs<T, Q1, TY>() * fd_group<T, Q1, TY>() * ((FD_TX + 1) * TY + FD_TX * (TY + 1))) +
            sizeof(double) * (FD_TX * TY / 32) * NOBS;
 }
 
@@ -159,10 +168,11 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     constexpr int VEC = 16 / sizeof(T);   // values per 16-byte copy
     constexpr int RV = HXP / VEC;         // 16-byte chunks per staged row
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int G = fd_group<T, Q1>();
+    constexpr int G = fd_group<T, Q1, TY>();
+    constexpr int FB = fd_face_bufs<T, Q1, TY>();
     T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
-    T* faces = tiles + (size_t)K * HXY;                  // [2][G][NF]
-    double* red = reinterpret_cast<double*>(faces + 2 * G * NF);
+    T* faces = tiles + (size_t)K * HXY;                  // [FB][G][NF]
+    double* red = reinterpret_cast<double*>(faces + FB * G * NF);
     __shared__ long long s_row[HY];                      // wrapped row offsets (edge tiles)
     __shared__ int s_col[HXP];                           // wrapped columns (edge tiles)
     __shared__ int s_obs;                                // record observables for this item
@@ -340,12 +350,15 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
 
         // 3. per group of G populations: every thread evaluates the x- and
         //    y-face on the low side of its node for each population of the
-        //    group (one packed pair each), warps 0..G-1 add the edge faces,
-        //    one barrier, then every node updates those G populations from
-        //    the four faces around it. Face buffers alternate between groups.
+        //    group (one packed pair each), warp p mod TY adds the edge faces
+        //    of the group's p-th population, one barrier, then every node
+        //    updates those G populations from the four faces around it. Two
+        //    face buffers alternate between groups; with one, a barrier also
+        //    precedes each group's faces.
 #pragma unroll
         for (int k0 = 0; k0 < K; k0 += G) {
-            T* fg = faces + ((k0 / G) & 1) * G * NF;
+            T* fg = faces + (FB == 2 ? ((k0 / G) & 1) * G * NF : 0);
+            if (FB == 1 && k0 > 0) __syncthreads();  // the previous group's update is done with the faces
             T fnv[G];
 #pragma unroll
             for (int p = 0; p < G; ++p) {
