@@ -10,6 +10,7 @@ import concurrent.futures as cf
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 
@@ -53,14 +54,29 @@ KERNEL_SOURCES = {
 SHARED_SOURCES = ["common.cuh", "ptx.cuh", "kernels.h"]
 
 
-def kernel_digest(kernel: str) -> str:
-    """Digest of one kernel's sources and the headers it includes (identifies
-    the build a profile of that kernel was taken on)."""
+_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"', re.S)
+
+
+def code_text(src: str) -> str:
+    """Source text without comments and with whitespace runs collapsed, so
+    that a digest changes with the code only."""
+    s = _TOKENS.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", src)
+    return re.sub(r"\s+", " ", s).strip()
+
+
+def kernel_digest(kernel: str, read=None) -> str:
+    """Digest of the code of one kernel's sources and the headers it includes
+    (identifies the build a profile of that kernel was taken on; comments and
+    layout do not count). `read(name)` returns a file's text (default: the
+    working tree)."""
+    if read is None:
+        def read(name):
+            with open(os.path.join(CSRC, name), encoding="utf-8") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel] + SHARED_SOURCES:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+        h.update(f.encode())
+        h.update(code_text(read(f)).encode())
     return h.hexdigest()[:16]
 
 

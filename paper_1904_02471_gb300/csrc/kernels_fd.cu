@@ -11,6 +11,7 @@
 //   1. every population plane of the stage input is staged in shared memory
 //      with a periodic halo of 3 nodes (the WENO-5 stencil reach); the
 //      moments come from there,
+//   then per group of G populations:
 //   2. per group of G populations, every interface value is computed once
 //      and stored: (TX+1) x TY faces normal to x and TX x (TY+1) normal to y
 //      (a face is shared by the two nodes it separates, which also makes the
@@ -149,8 +150,8 @@ __host__ __device__ constexpr size_t fd_smem_bytes() {
 
 // Resident blocks per SM the register allocation is bounded for: 1024
 // threads per SM for FP32, i.e. at most 64 registers per thread (shared
-// memory, about 40 KiB per 256-thread block for 16 populations, allows as
-// many); 512 threads (128 registers) for FP64.
+// memory, 53.5 KiB per 256-thread block for 16 populations, allows as many:
+// four blocks in 228 KiB); 512 threads (128 registers) for FP64.
 template <typename T, int TY>
 constexpr int fd_min_blocks() { return (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) > 0 ? (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) : 1; }
 

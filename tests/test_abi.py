@@ -124,3 +124,18 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         lbm.lib()
+
+
+def test_kernel_digest_follows_code_not_comments():
+    """The digest that ties a recorded DRAM-traffic figure to a kernel's
+    sources ignores comments and layout, and changes with the code."""
+    from paper_1904_02471_gb300 import build
+    base = {"kernels_fd.cu": "int f(int a) { return a + 1; } // one\n", "common.cuh": "/* c */ #define X 1\n",
+            "ptx.cuh": 'const char* s = "a // not a comment";\n', "kernels.h": ""}
+    d0 = build.kernel_digest("fd_stage", base.__getitem__)
+    relaid = dict(base, **{"kernels_fd.cu": "// header\nint f(int a)\n{\n    return a + 1;  /* two */\n}\n"})
+    assert build.kernel_digest("fd_stage", relaid.__getitem__) == d0
+    changed = dict(base, **{"kernels_fd.cu": "int f(int a) { return a + 2; }\n"})
+    assert build.kernel_digest("fd_stage", changed.__getitem__) != d0
+    in_string = dict(base, **{"ptx.cuh": 'const char* s = "a // now different";\n'})
+    assert build.kernel_digest("fd_stage", in_string.__getitem__) != d0
