@@ -361,8 +361,14 @@ typedef struct lbm_server lbm_server;
 
 /* Start a server with a worker thread. hbm_budget_bytes bounds the summed
  * device footprint of resident runs (admission control); max_slots bounds
- * their number; chunk_steps is the number of steps per scheduling round.
- * cuda_stream as in lbm_create. A server is thread-safe. */
+ * their number. Resident runs advance together in scheduling rounds that give
+ * each run about the same device time: the run with the cheapest step (by an
+ * estimate from its lattice size, model, velocity set and precision) advances
+ * chunk_steps steps per round, a run whose step costs m times as much
+ * advances chunk_steps / m (at least 1), none more than it has left; so a
+ * small run is not held to the pace of a large one. Requests admitted while
+ * others run join at the next round. cuda_stream as in lbm_create. A server
+ * is thread-safe. */
 int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, int chunk_steps,
                       void* cuda_stream);
 /* Queue a request and return at once with its ticket. LBM_EINVAL / LBM_ECFL /

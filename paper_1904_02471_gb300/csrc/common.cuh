@@ -174,6 +174,15 @@ __device__ __forceinline__ int find_lattice(const int* __restrict__ item_begin, 
     return lo;
 }
 
+// Last item of this block's sequence (first item `item`, stride gridDim.x)
+// that still belongs to lattice d. A lattice that sits out a step (its step
+// budget is spent) is passed over in one jump: the item loop continues from
+// there, so its tiles cost nothing however many there are.
+__device__ __forceinline__ int last_item_of(const LatDesc& d, int item) {
+    const int stride = (int)gridDim.x;
+    return item + (d.item_begin + d.items - 1 - item) / stride * stride;
+}
+
 // Observe the state at sub-step j of this chunk?
 __device__ __forceinline__ bool observe_now(const LatDesc& d, int j) {
     if (d.obs_every <= 0) return false;

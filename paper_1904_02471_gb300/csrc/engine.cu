@@ -843,6 +843,23 @@ int Engine::set_budget(int i, long long steps) {
     return upload_group(lat[i].group);
 }
 
+int Engine::set_budgets(const std::vector<std::pair<int, long long>>& budgets) {
+    for (const auto& b : budgets)
+        if (!valid(b.first) || b.second < 0) { set_error("bad budget"); return LBM_EINVAL; }
+    CK(cudaStreamSynchronize(stream_));
+    std::vector<char> touched(groups.size(), 0);
+    for (const auto& b : budgets) {
+        lat[b.first].remaining = b.second;
+        touched[lat[b.first].group] = 1;
+    }
+    for (int gi = 0; gi < (int)groups.size(); ++gi)
+        if (touched[gi]) {
+            const int rc = upload_group(gi);
+            if (rc) return rc;
+        }
+    return LBM_OK;
+}
+
 int Engine::release_io(int i) {
     if (!valid(i)) { set_error("bad arguments"); return LBM_EINVAL; }
     CK(cudaStreamSynchronize(stream_));

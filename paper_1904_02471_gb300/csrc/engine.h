@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "kernels.h"
@@ -131,6 +132,8 @@ class Engine {
     int record(int i, long long every, long long cap);
     int series(int i, lbm_obs* out, long long cap, long long* count);
     int set_budget(int i, long long steps);
+    // Several budgets at once: one upload per group touched.
+    int set_budgets(const std::vector<std::pair<int, long long>>& budgets);
     int release_io(int i);   // free the staging buffer of init / readout
     int set_eps(int i, double eps);
     size_t checkpoint_size(int i) const;

@@ -116,7 +116,10 @@ __global__ void __launch_bounds__(TX) cs_step_kernel(GroupDev g, int j) {
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int li = find_lattice(g.item_begin, n_lat, item);
         const LatDesc* dp = g.desc + li;
-        if ((long long)j >= dp->remaining) continue;
+        if ((long long)j >= dp->remaining) {
+            item = last_item_of(*dp, item);
+            continue;
+        }
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const long long plane = dp->plane;
         const int local = item - dp->item_begin;
@@ -398,7 +401,10 @@ __global__ void __launch_bounds__(32 + W, cs_bulk_min_blocks<T, W>()) cs_bulk_ke
         for (int item = blockIdx.x; item < total && ok; item += gridDim.x) {
             const int li = find_lattice(g.item_begin, n_lat, item);
             const LatDesc* dp = g.desc + li;
-            if ((long long)j >= dp->remaining) continue;
+            if ((long long)j >= dp->remaining) {
+                item = last_item_of(*dp, item);
+                continue;
+            }
             const int ny = dp->ny, pitch = dp->pitch;
             const long long plane = dp->plane;
             const int local = item - dp->item_begin;
@@ -432,7 +438,10 @@ __global__ void __launch_bounds__(32 + W, cs_bulk_min_blocks<T, W>()) cs_bulk_ke
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int li = find_lattice(g.item_begin, n_lat, item);
         const LatDesc* dp = g.desc + li;
-        if ((long long)j >= dp->remaining) continue;
+        if ((long long)j >= dp->remaining) {
+            item = last_item_of(*dp, item);
+            continue;
+        }
         const int nx = dp->nx, ny = dp->ny;
         const int local = item - dp->item_begin;
         const int bx = local % dp->tiles_x, by = local / dp->tiles_x;

@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int li = find_lattice(g.item_begin, n_lat, item);
         const LatDesc* dp = g.desc + li;
-        if ((long long)j >= dp->remaining) continue;
+        if ((long long)j >= dp->remaining) {
+            item = last_item_of(*dp, item);
+            continue;
+        }
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const long long plane = dp->plane;
         const int local = item - dp->item_begin;

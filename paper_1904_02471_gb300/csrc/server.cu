@@ -3,13 +3,16 @@
 // Requests are complete runs (model, lattice, tau, steps, initial state).
 // One worker thread owns a dynamic Engine: it admits queued requests as
 // slots and device memory (an HBM budget on the summed lattice footprints)
-// free up, advances every resident run together in rounds of chunk_steps
-// (one captured CUDA-graph replay per 32 steps, runs that reach their step
-// budget are skipped by the kernels), and retires finished runs at the end of
-// a round: final observables, recorded series, fitted apparent viscosity,
-// then the lattice's memory is released and waiting requests are admitted.
+// free up, advances every resident run together in rounds that give each
+// run about the same device time (the cheapest run advances chunk_steps
+// steps, costlier ones proportionally fewer; one captured CUDA-graph replay
+// per 32 steps, runs that have spent their allotment are skipped by the
+// kernels), and retires finished runs at the end of a round: final
+// observables, recorded series, fitted apparent viscosity, then the lattice's
+// memory is released and waiting requests are admitted.
 // Requests that arrive while others are on the GPU join at the next round,
 // so their work overlaps on the device.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -31,6 +34,7 @@ struct Req {
     double t_submit = 0, t_admit = -1, t_done = -1;
     int state = 0;  // 0 queued, 1 running, 2 done
     int lat = -1;
+    long long left = 0;  // steps still to run (worker thread only)
     size_t bytes = 0;
     bool cancel = false;
     lbm_result res{};
@@ -61,6 +65,20 @@ void initial_fields(const lbm_request& q, std::vector<double>& rho, std::vector<
                 rho[c] = x <= nx / 2 ? q.rho_l : q.rho_r;
             }
         }
+}
+
+// Estimated device time of one step of a run alone, for sharing the device
+// between runs: about 20 us of fixed cost per step (launch and tile latency
+// of a small lattice) plus a cost per node, from single-lattice rates on
+// GB300 (FP32: CS D2Q9 in place 74 GLUPS, FD 16-velocity 4.4 GLUPS, the FD
+// cost scaled by the number of velocities; FP64 on the narrow FP64 pipe).
+// Only the ratios between runs matter.
+double step_cost(const lbm_spec& s) {
+    const double nodes = (double)s.nx * s.ny;
+    const double k = (double)s.q_per_axis * s.q_per_axis;
+    const double per_node = s.model == LBM_CS ? (s.precision == LBM_FP64 ? 0.125e-9 : 0.0135e-9)
+                                              : (s.precision == LBM_FP64 ? 6e-9 : 0.227e-9) * k / 16.0;
+    return 20e-6 + nodes * per_node;
 }
 
 }  // namespace
@@ -124,7 +142,8 @@ struct lbm_server {
         }
         rc = e.release_io(idx);  // only the state stays resident (the budget counts it)
         if (rc) return rc;
-        return e.set_budget(idx, q.r.steps);
+        q.left = q.r.steps;
+        return e.set_budget(idx, 0);  // steps are allotted round by round
     }
 
     // Results of a run whose budget is exhausted (worker thread, no lock).
@@ -209,19 +228,44 @@ struct lbm_server {
                 rc = e.inject_wait_timeout(want);
                 inject_applied = want;
             }
-            if (rc == LBM_OK) rc = e.step(chunk);
+            // One round: every resident run gets about the same device time.
+            // The cheapest run (by step_cost) advances `chunk` steps, a run
+            // whose step costs m times as much advances chunk / m steps (at
+            // least one), none more than it has left. Runs that finish their
+            // allotment early sit out the rest of the round.
+            std::vector<Req*> rq;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                for (uint64_t t : running) rq.push_back(&reqs[t]);
+            }
+            std::vector<long long> steps(rq.size(), 0);
+            long long round_steps = 0;
+            if (rc == LBM_OK) {
+                double cmin = 1e300;
+                std::vector<double> cost(rq.size());
+                for (size_t i = 0; i < rq.size(); ++i) cmin = std::min(cmin, cost[i] = step_cost(rq[i]->r.spec));
+                std::vector<std::pair<int, long long>> budgets;
+                for (size_t i = 0; i < rq.size(); ++i) {
+                    const long long share = std::max(1LL, std::llround(chunk * cmin / cost[i]));
+                    steps[i] = std::min(std::min<long long>(chunk, share), rq[i]->left);
+                    round_steps = std::max(round_steps, steps[i]);
+                    budgets.emplace_back(rq[i]->lat, steps[i]);
+                }
+                rc = e.set_budgets(budgets);
+            }
+            if (rc == LBM_OK) rc = e.step(round_steps);
             if (rc == LBM_OK) rc = e.sync();
             std::vector<uint64_t> still;
-            for (uint64_t t : running) {
-                Req* q;
+            for (size_t i = 0; i < rq.size(); ++i) {
+                const uint64_t t = running[i];
+                Req* q = rq[i];
                 bool cancel;
                 {
                     std::lock_guard<std::mutex> lk(mu);
-                    q = &reqs[t];
                     cancel = q->cancel || stop;
                 }
-                const lbm::Lattice& L = e.L(q->lat);
-                if (rc == LBM_OK && !cancel && L.remaining > 0) {
+                if (rc == LBM_OK) q->left -= steps[i];
+                if (rc == LBM_OK && !cancel && q->left > 0) {
                     still.push_back(t);
                     continue;
                 }

@@ -1,9 +1,11 @@
 """The continuous-batching run server (lbm_server_*) on the GPU.
 
 Each run gives the same result alone and in a mix of concurrent runs;
-admission follows the memory budget and the slot count; runs that arrive
-while others are on the GPU start before those finish; cancellation; and the
-fitted apparent viscosity of a shear wave matches Eq. (nulu).
+rounds share device time, so a cheap run is not held to the pace of an
+expensive one; admission follows the memory budget and the slot count; runs
+that arrive while others are on the GPU start before those finish;
+cancellation; and the fitted apparent viscosity of a shear wave matches
+Eq. (nulu).
 """
 import math
 import time
@@ -148,3 +150,17 @@ def test_shear_wave_viscosity_fit():
     nu = pkg.lbm_nu(lbm.LBM_CS, tau, 1 / SQ3)
     assert r["status"] == lbm.LBM_OK
     assert abs(r["nu_fit"] / nu - 1) < 2e-3, r["nu_fit"] / nu
+
+
+def test_cheap_run_is_not_held_to_the_pace_of_an_expensive_one():
+    """Rounds share device time, not steps: a cheap run (CS 64^2) with more
+    steps than an expensive one (FD 16-velocity 1024^2), submitted after it,
+    finishes first. With rounds of equal steps it would finish last."""
+    with lbm.Server(8 * GB, 8, 32) as S:
+        t_long = S.submit(lbm.make_request(_fd(1024, 4), 300, "tg", 0.01))
+        t_short = S.submit(lbm.make_request(_cs(64, 0.6), 1000, "tg", 0.01 * SQ3))
+        S.drain(300)
+        rl, rs = S.poll(t_long), S.poll(t_short)
+    assert rl["status"] == rs["status"] == lbm.LBM_OK
+    assert rl["steps"] == 300 and rs["steps"] == 1000
+    assert rs["t_done"] < rl["t_done"], (rs["t_done"], rl["t_done"])
