@@ -171,6 +171,13 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = fd_group<T, Q1, TY>();
     constexpr int FB = fd_face_bufs<T, Q1, TY>();
+    // 16-velocity set: populations 2q and 2q+1 (nodes ix = 0, 1 or 2, 3 of
+    // one row of the product set) have the same signs of both velocity
+    // components, so the same upwind stencils: their faces are evaluated and
+    // stored side by side
+    constexpr bool PAIRS = Q1 == 4;
+    static_assert(!PAIRS || (GH<4>::v(0) < 0 && GH<4>::v(1) < 0 && GH<4>::v(2) > 0 && GH<4>::v(3) > 0 && G % 2 == 0),
+                  "pairs (2q, 2q+1) must share their upwind directions");
     T* tiles = reinterpret_cast<T*>(smem_raw);          // [K][HY][HXP]
     T* faces = tiles + (size_t)K * HXY;                  // [FB][G][NF]
     double* red = reinterpret_cast<double*>(faces + FB * G * NF);
@@ -358,45 +365,84 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         //    of the group's p-th population, one barrier, then every node
         //    updates those G populations from the four faces around it. Two
         //    face buffers alternate between groups; with one, a barrier also
-        //    precedes each group's faces.
+        //    precedes each group's faces. With the 16-velocity set the packed
+        //    pairs are two populations' x-faces and then their y-faces instead
+        //    of one population's x- and y-face, and faces are stored and read
+        //    back as pairs (half the shared-memory instructions for them).
 #pragma unroll
         for (int k0 = 0; k0 < K; k0 += G) {
             T* fg = faces + (FB == 2 ? ((k0 / G) & 1) * G * NF : 0);
             if (FB == 1 && k0 > 0) __syncthreads();  // the previous group's update is done with the faces
             T fnv[G];
+            if constexpr (PAIRS) {
+                // populations 2q and 2q+1 of the group side by side: the x-faces
+                // of both as one packed pair, then the y-faces of both; faces
+                // stored as pairs [TY][TX + 1] and [TY + 1][TX] of V per q
 #pragma unroll
-            for (int p = 0; p < G; ++p) {
-                const int k = k0 + p;
-                if (k >= K) break;
-                const T* tk = tiles + k * HXY;
-                T* fx = fg + p * NF;            // [TY][TX + 1]
-                T* fy = fx + NFX;               // [TY + 1][TX]
-                const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
-                // upwind stencil of the face on the low side of node (c, r):
-                // x, v > 0: cols c+1..c+5 of row r+3; v < 0: cols c+6..c+2
-                // y, v > 0: rows r..r+4 of col c+4; v < 0: rows r+5..r+1
-                const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
-                const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
-                {
-                    const T* px = tk + xrow + xo;
-                    const T* py = tk + ycol + yo;
-                    const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
-                                              P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
-                    fx[ty * (TX + 1) + tx] = f.x;
-                    fy[ty * TX + tx] = f.y;
+                for (int q = 0; q < G / 2; ++q) {
+                    const int ka = k0 + 2 * q;
+                    const T* ta = tiles + ka * HXY;
+                    const T* tb = ta + HXY;
+                    V* fx2 = reinterpret_cast<V*>(fg) + q * NF;
+                    V* fy2 = fx2 + NFX;
+                    const double vxd = vx_of<Q1>(ka), vyd = vy_of<Q1>(ka);   // also the signs of ka + 1
+                    const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
+                    const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
+                    auto face = [&](int base, int o, int st) {
+                        const T* a = ta + base + o;
+                        const T* b = tb + base + o;
+                        return weno5_pair<T>(P::mk(a[0], b[0]), P::mk(a[st], b[st]), P::mk(a[2 * st], b[2 * st]),
+                                             P::mk(a[3 * st], b[3 * st]), P::mk(a[4 * st], b[4 * st]), eps);
+                    };
+                    fx2[ty * (TX + 1) + tx] = face(xrow, xo, xs);
+                    fy2[ty * TX + tx] = face(ycol, yo, ys);
+                    if (ty == (2 * q) % TY) {
+                        const V f = face(exrow, xo, xs);
+                        if (tx < TY) fx2[tx * (TX + 1) + TX] = f;
+                    }
+                    if (ty == (2 * q + 1) % TY) fy2[TY * TX + tx] = face(eycol, yo, ys);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = ka + h;
+                        fnv[2 * q + h] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
+                    }
                 }
-                if (ty == p % TY) {
-                    const T* px = tk + exrow + xo;
-                    const T* py = tk + eycol + yo;
-                    const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
-                                              P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
-                    if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
-                    fy[TY * TX + tx] = f.y;
+            } else {
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    const int k = k0 + p;
+                    if (k >= K) break;
+                    const T* tk = tiles + k * HXY;
+                    T* fx = fg + p * NF;            // [TY][TX + 1]
+                    T* fy = fx + NFX;               // [TY + 1][TX]
+                    const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
+                    // upwind stencil of the face on the low side of node (c, r):
+                    // x, v > 0: cols c+1..c+5 of row r+3; v < 0: cols c+6..c+2
+                    // y, v > 0: rows r..r+4 of col c+4; v < 0: rows r+5..r+1
+                    const int xo = vxd > 0 ? 1 : 6, xs = vxd > 0 ? 1 : -1;
+                    const int yo = vyd > 0 ? 0 : 5 * HXP, ys = vyd > 0 ? HXP : -HXP;
+                    {
+                        const T* px = tk + xrow + xo;
+                        const T* py = tk + ycol + yo;
+                        const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                                  P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                        fx[ty * (TX + 1) + tx] = f.x;
+                        fy[ty * TX + tx] = f.y;
+                    }
+                    if (ty == p % TY) {
+                        const T* px = tk + exrow + xo;
+                        const T* py = tk + eycol + yo;
+                        const V f = weno5_pair<T>(P::mk(px[0], py[0]), P::mk(px[xs], py[ys]), P::mk(px[2 * xs], py[2 * ys]),
+                                                  P::mk(px[3 * xs], py[3 * ys]), P::mk(px[4 * xs], py[4 * ys]), eps);
+                        if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
+                        fy[TY * TX + tx] = f.y;
+                    }
+                    fnv[p] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
                 }
-                fnv[p] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
             }
             __syncthreads();
             if (active) {
+                V pxl, pxr, pyb, pyt;   // face pairs of populations 2q, 2q+1 (PAIRS)
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
                     const int k = k0 + p;
@@ -405,6 +451,27 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     const T* fx = fg + p * NF;
                     const T* fy = fx + NFX;
                     const double vxd = vx_of<Q1>(k), vyd = vy_of<Q1>(k);
+                    // the four faces around the node: low/high x, low/high y
+                    T fxl, fxh, fyl, fyh;
+                    if constexpr (PAIRS) {
+                        if ((p & 1) == 0) {
+                            const V* fx2 = reinterpret_cast<const V*>(fg) + (p >> 1) * NF;
+                            const V* fy2 = fx2 + NFX;
+                            pxl = fx2[ty * (TX + 1) + tx];
+                            pxr = fx2[ty * (TX + 1) + tx + 1];
+                            pyb = fy2[ty * TX + tx];
+                            pyt = fy2[(ty + 1) * TX + tx];
+                        }
+                        fxl = (p & 1) ? pxl.y : pxl.x;
+                        fxh = (p & 1) ? pxr.y : pxr.x;
+                        fyl = (p & 1) ? pyb.y : pyb.x;
+                        fyh = (p & 1) ? pyt.y : pyt.x;
+                    } else {
+                        fxl = fx[ty * (TX + 1) + tx];
+                        fxh = fx[ty * (TX + 1) + tx + 1];
+                        fyl = fy[ty * TX + tx];
+                        fyh = fy[(ty + 1) * TX + tx];
+                    }
                     // flux difference F(i+1/2) - F(i-1/2) = (c+ - c-) + (d+ - d-)/12:
                     // the upwind node values c differ by one node (exact for
                     // close values), the stored corrections d = 12 (face - c) are small
@@ -414,11 +481,11 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     T a = T(0);
                     if (vxd != 0.0) {
                         const T dc = vxd > 0 ? uk - tk[cidx - 1] : tk[cidx + 1] - uk;
-                        a = vx * ((fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * T(1.0 / 12.0) + dc);
+                        a = vx * ((fxh - fxl) * T(1.0 / 12.0) + dc);
                     }
                     if (vyd != 0.0) {
                         const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
-                        a += vy * ((fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * T(1.0 / 12.0) + dc);
+                        a += vy * ((fyh - fyl) * T(1.0 / 12.0) + dc);
                     }
                     const T xi = vx * ux + vy * uy;
                     const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jxc + (vy * jyc + drc)));
