@@ -139,3 +139,19 @@ def test_kernel_digest_follows_code_not_comments():
     assert build.kernel_digest("fd_stage", changed.__getitem__) != d0
     in_string = dict(base, **{"ptx.cuh": 'const char* s = "a // now different";\n'})
     assert build.kernel_digest("fd_stage", in_string.__getitem__) != d0
+
+
+def test_recorded_dram_traffic_matches_the_kernel_sources():
+    """Every DRAM-traffic entry under profiles/ was taken on the kernel code
+    in the tree (its digest matches), and its bytes are within 10% of the
+    algorithmic bytes, as the profile summaries state."""
+    import json
+    import os
+    from paper_1904_02471_gb300 import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "profiles", "traffic.json")) as fh:
+        rec = json.load(fh)
+    assert set(rec["kernels"]) == set(build.KERNEL_SOURCES)
+    for name, e in rec["kernels"].items():
+        assert e["source_digest"] == build.kernel_digest(name), name
+        assert 0.9 < e["bytes_per_launch"] / e["algorithmic_bytes_per_launch"] <= 1.1, name
