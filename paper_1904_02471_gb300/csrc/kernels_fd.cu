@@ -233,11 +233,11 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         // SK-th population, stepping by whole planes (no index arithmetic per
         // copy); row_src(r, c) is the source of population 0
         auto stage_rows16 = [&](int t, auto row_src) {
-            constexpr int PAIRS = HY * RV;
-            if constexpr (NT >= PAIRS) {
-                constexpr int SK = NT / PAIRS;
-                if (t < SK * PAIRS) {
-                    const int pr = t % PAIRS, k0 = t / PAIRS;
+            constexpr int CHUNKS = HY * RV;   // (row, 16-byte chunk) positions of a tile
+            if constexpr (NT >= CHUNKS) {
+                constexpr int SK = NT / CHUNKS;
+                if (t < SK * CHUNKS) {
+                    const int pr = t % CHUNKS, k0 = t / CHUNKS;
                     const int r = pr / RV, c = pr - r * RV;
                     const T* sp = row_src(r, c) + k0 * plane;
                     T* dp16 = tiles + k0 * HXY + r * HXP + c * VEC;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                         if (LBM_BC_NODE(dp, K, sp - U) && LBM_BC_NODE(dp, K, sp - U + VEC - 1)) cp_async16(dp16, sp);
                 }
             } else {
-                for (int pr = t; pr < PAIRS; pr += NT) {
+                for (int pr = t; pr < CHUNKS; pr += NT) {
                     const int r = pr / RV, c = pr - r * RV;
                     const T* sp = row_src(r, c);
                     T* dp16 = tiles + r * HXP + c * VEC;
