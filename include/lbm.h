@@ -368,7 +368,9 @@ typedef struct lbm_server lbm_server;
  * advances chunk_steps / m (at least 1), none more than it has left; so a
  * small run is not held to the pace of a large one. Requests admitted while
  * others run join at the next round. cuda_stream as in lbm_create. A server
- * is thread-safe. */
+ * is thread-safe. LBM_EINVAL for a null out, a zero budget, max_slots < 1 or
+ * chunk_steps < 1; LBM_ENOMEM or LBM_ECUDA if the engine cannot be set up
+ * (*out is then null). */
 int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, int chunk_steps,
                       void* cuda_stream);
 /* Queue a request and return at once with its ticket. LBM_EINVAL / LBM_ECFL /
