@@ -301,8 +301,9 @@ int lbm_batch_groups(lbm_batch* b, int* model, int* q, int* precision, int cap);
 int lbm_batch_step_profiled(lbm_batch* b, int64_t n, double* ms, int cap, double* total_ms);
 
 /* Kernel configuration of group `group` of a batch (lbm_batch_groups order):
- * tile variant 0 .. lbm_n_tiles(model)-1 and persistent grid size (0 picks
- * one CTA set per SM from occupancy). Every variant computes bit-identical
+ * tile variant 0 .. lbm_n_tiles(model)-1 and grid size (blocks loop over the
+ * group's work items; 0 picks the default: one block per work item, i.e. per
+ * tile of every lattice of the group). Every variant computes bit-identical
  * results; only speed differs. lbm_config does the same for a context. */
 int lbm_batch_config(lbm_batch* b, int group, int tile, int grid);
 int lbm_config(lbm_ctx* ctx, int tile, int grid);

@@ -81,7 +81,7 @@ int Engine::tune(int trial_steps, std::string* report) {
             if (rc) return rc;
             g.any_obs = false;
             const int full = g.total_items;
-            const int pers = default_grid(g, t);
+            const int pers = std::min(full, persistent_grid(g, t));
             const int cands[3] = {pers, std::min(full, 2 * pers), full};
             for (int ci = 0; ci < 3; ++ci) {
                 const int grid = std::max(1, cands[ci]);

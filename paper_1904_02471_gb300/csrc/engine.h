@@ -146,6 +146,7 @@ class Engine {
     Group& G(int g) { return groups[g]; }
     int sm_count() const { return sm_count_; }
     int default_grid(const Group& g, int tile) const;
+    int persistent_grid(const Group& g, int tile) const;
     int tune(int trial_steps, std::string* report);
 
     int chunk = 32;          // steps per captured graph

@@ -7,7 +7,7 @@ Each case is a Taylor-Green lattice in FP32 deviation storage whose state is
 larger than the 129 MB L2 (CS 2048^2: 302 MB; FD 16-velocity 1024^2: 201 MB),
 so DRAM counters mean what they say, yet small enough that a multi-pass
 capture ends in seconds. The kernel variant can be pinned with --tile, the
-grid with --grid (0: one persistent block per resident slot; the benchmark's
+grid with --grid (0: the default, one block per tile; the benchmark's
 tuner picks one block per tile for the FD stage).
 """
 from __future__ import annotations
