@@ -1,4 +1,4 @@
-// Autotuner: picks the tile shape and persistent grid size of every group by
+// Autotuner: picks the tile shape and grid size of every group by
 // timing each candidate on the group's own lattices (state saved and
 // restored around the trials). Results are cached per (model, q, precision,
 // storage, work-size class) for the life of the process.
