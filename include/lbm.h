@@ -394,6 +394,14 @@ int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* 
                      size_t* resident_bytes);
 /* Cancel what is left, stop the worker and free everything. */
 void lbm_server_destroy(lbm_server* s);
+/* The steps each of n runs advances in one scheduling round of a server with
+ * chunk_steps (the rule of lbm_server_create): specs[i] the run's lattice,
+ * left[i] >= 0 the steps it has still to run; steps[i] receives its
+ * allotment (0 only when left[i] is 0). Host arrays, caller-owned; no device
+ * work. For callers that schedule their own batches (lbm_batch_set_budget)
+ * the same way. LBM_EINVAL for n < 0, chunk_steps < 1, a null array with
+ * n > 0 or a negative left[i]; a bad spec returns what lbm_create returns. */
+int lbm_server_plan_round(const lbm_spec* specs, const int64_t* left, int n, int chunk_steps, int64_t* steps);
 
 /* Test injection of a device-side wait that runs out (no counterpart in the
  * paper; failure detection of the library itself). The CS bulk-copy kernel

@@ -81,6 +81,18 @@ double step_cost(const lbm_spec& s) {
     return 20e-6 + nodes * per_node;
 }
 
+// Steps of one scheduling round (see lbm_server_create): the run with the
+// cheapest step advances `chunk` steps, a run whose step costs m times as
+// much chunk / m (at least one), none more than it has left.
+void plan_round(const double* cost, const long long* left, size_t n, int chunk, long long* steps) {
+    double cmin = 1e300;
+    for (size_t i = 0; i < n; ++i) cmin = std::min(cmin, cost[i]);
+    for (size_t i = 0; i < n; ++i) {
+        const long long share = std::max(1LL, std::llround(chunk * cmin / cost[i]));
+        steps[i] = std::min(std::min<long long>(chunk, share), left[i]);
+    }
+}
+
 }  // namespace
 
 struct lbm_server {
@@ -241,13 +253,15 @@ struct lbm_server {
             std::vector<long long> steps(rq.size(), 0);
             long long round_steps = 0;
             if (rc == LBM_OK) {
-                double cmin = 1e300;
                 std::vector<double> cost(rq.size());
-                for (size_t i = 0; i < rq.size(); ++i) cmin = std::min(cmin, cost[i] = step_cost(rq[i]->r.spec));
+                std::vector<long long> left(rq.size());
+                for (size_t i = 0; i < rq.size(); ++i) {
+                    cost[i] = step_cost(rq[i]->r.spec);
+                    left[i] = rq[i]->left;
+                }
+                plan_round(cost.data(), left.data(), rq.size(), chunk, steps.data());
                 std::vector<std::pair<int, long long>> budgets;
                 for (size_t i = 0; i < rq.size(); ++i) {
-                    const long long share = std::max(1LL, std::llround(chunk * cmin / cost[i]));
-                    steps[i] = std::min(std::min<long long>(chunk, share), rq[i]->left);
                     round_steps = std::max(round_steps, steps[i]);
                     budgets.emplace_back(rq[i]->lat, steps[i]);
                 }
@@ -382,6 +396,34 @@ int lbm_cancel(lbm_server* s, uint64_t ticket) {
         q.cancel = true;
     }
     return LBM_OK;
+}
+
+int lbm_server_plan_round(const lbm_spec* specs, const int64_t* left, int n, int chunk_steps, int64_t* steps) {
+    if (n < 0 || chunk_steps < 1 || (n > 0 && (!specs || !left || !steps))) {
+        lbm::set_error("plan_round needs n >= 0, chunk_steps >= 1 and the arrays");
+        return LBM_EINVAL;
+    }
+    try {
+        std::vector<double> cost((size_t)n);
+        std::vector<long long> l((size_t)n), out((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            lbm_spec norm;
+            const int rc = lbm::Engine::validate(&specs[i], &norm);
+            if (rc) return rc;
+            if (left[i] < 0) {
+                lbm::set_error("negative steps left");
+                return LBM_EINVAL;
+            }
+            cost[(size_t)i] = step_cost(norm);
+            l[(size_t)i] = left[i];
+        }
+        plan_round(cost.data(), l.data(), (size_t)n, chunk_steps, out.data());
+        for (int i = 0; i < n; ++i) steps[i] = out[(size_t)i];
+        return LBM_OK;
+    } catch (...) {
+        lbm::set_error("plan_round failed");
+        return LBM_ENOMEM;
+    }
 }
 
 int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds) {

@@ -145,6 +145,7 @@ _SIGS = [
     ("lbm_server_stats", _i, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                               ctypes.POINTER(_sz)]),
     ("lbm_server_destroy", None, [_P]),
+    ("lbm_server_plan_round", _i, [ctypes.POINTER(lbm_spec), ctypes.POINTER(_i64), _i, _i, ctypes.POINTER(_i64)]),
     ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, _d, _i, _P, _P, _d, _i64, _d,
                                      _P, _P]),
 ]
@@ -507,6 +508,16 @@ def make_request(spec: lbm_spec, steps, init="tg", U=0.01, obs_every=0, rho_l=1.
     r.U, r.rho_l, r.rho_r = U, rho_l, rho_r
     r.user_tag = tag
     return r
+
+
+def plan_round(specs, left, chunk_steps):
+    """Steps each run advances in one server round (lbm_server_plan_round)."""
+    n = len(specs)
+    arr = (lbm_spec * max(n, 1))(*specs)
+    lft = (_i64 * max(n, 1))(*[int(v) for v in left])
+    out = (_i64 * max(n, 1))()
+    check(lib().lbm_server_plan_round(arr, lft, n, int(chunk_steps), out), "lbm_server_plan_round")
+    return [int(out[i]) for i in range(n)]
 
 
 class Server:

@@ -155,3 +155,37 @@ def test_recorded_dram_traffic_matches_the_kernel_sources():
     for name, e in rec["kernels"].items():
         assert e["source_digest"] == build.kernel_digest(name), name
         assert 0.9 < e["bytes_per_launch"] / e["algorithmic_bytes_per_launch"] <= 1.1, name
+
+
+def test_server_round_plan():
+    """The server's round allotment (host logic, no GPU): equal device time per
+    run by the step-cost estimate, at least one step, never more than left."""
+    import math
+    import paper_1904_02471_gb300 as pkg
+    from paper_1904_02471_gb300 import lbm
+    sq3 = math.sqrt(3.0)
+
+    def fd(n):
+        tau = pkg.lbm_tau_fd_from_lu(n, 0.9 / sq3)
+        return pkg.make_spec("fd", 4, n, n, tau, min(tau, 0.4 * pkg.lbm_fd_max_dt(4, 1.0 / n, 1e300)), 0.0, "fp32")
+
+    def cs(n, prec="fp32"):
+        return pkg.make_spec("cs", 3, n, n, 0.6, 0.0, 0.0, prec)
+
+    # FD 1024^2 step ~ 20 us + 1 M nodes x 0.227 ns, CS 64^2 ~ 20 us: ratio ~12.9 -> 32 / 12.9 = 2
+    assert lbm.plan_round([fd(1024), cs(64)], [300, 1000], 32) == [2, 32]
+    assert lbm.plan_round([fd(4096), cs(64)], [300, 1000], 32) == [1, 32]       # at least one
+    assert lbm.plan_round([fd(1024), cs(64)], [1, 5], 32) == [1, 5]             # never more than left
+    assert lbm.plan_round([cs(64), cs(64)], [0, 100], 32) == [0, 32]            # finished runs get none
+    assert lbm.plan_round([fd(4096)], [10 ** 6], 64) == [64]                    # a run alone: the chunk
+    assert lbm.plan_round([cs(256), cs(256)], [500, 500], 16) == [16, 16]       # equal costs, equal steps
+    a, b = lbm.plan_round([cs(2048), cs(2048, "fp64")], [10 ** 6, 10 ** 6], 64)
+    assert a == 64 and 1 <= b < a                                               # FP64 costs more
+    assert lbm.plan_round([], [], 8) == []
+    for args in (([cs(64)], [1], 0), ([cs(64)], [-1], 8)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.plan_round(*args)
+        assert e.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:                                      # a bad spec as in lbm_create
+        lbm.plan_round([pkg.make_spec("cs", 4, 64, 64, 0.6, 0.0, 0.0, "fp32")], [10], 8)
+    assert e.value.code == lbm.LBM_EINVAL
