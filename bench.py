@@ -10,10 +10,16 @@ nothing is flushed between steps.
 
 Metric: MLUPS (million lattice-node updates per second) over the workload,
 whole job (all ranks); per-kernel CUDA-event durations give the roofline
-fraction of the dominant kernel against the measured HBM copy bandwidth.
+fractions of the dominant kernel (the FD stage) against the FP32 peak and
+the measured HBM copy bandwidth. The same line carries the end-to-end rate
+through the public API (host fields in, observables out), the batched
+(256 mixed lattices, FP32 vs FP64 one at a time) and served (Poisson stream)
+legs, and the FP64 oracle's rate on every host core (cpu_baseline).
 
 --impl reference times the FP64 C oracle on the host cores instead (the
-paper publishes no implementation or timings), on bounded samples.
+paper publishes no implementation or timings), on bounded samples, one
+oracle process per core. --served-full N runs only the served stream in its
+full configuration (lattices 64^2..4096^2, 1k..20k steps; several minutes).
 Multi-GPU: replicas only (each rank advances its own copy; no collective on
 the data path).
 """
