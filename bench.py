@@ -172,8 +172,11 @@ def _oracle_worker(budget_s: float):
 
 def oracle_pool(nproc: int):
     """One worker process per host core for the oracle. Spawned, not forked:
-    no CUDA state of the parent is inherited."""
+    no CUDA state of the parent is inherited. The oracle library is built
+    once here first, so the workers only load it."""
     import multiprocessing as mp
+    from oracle import build as oracle_build
+    oracle_build.build()
     return mp.get_context("spawn").Pool(nproc)
 
 
