@@ -477,14 +477,16 @@ def check_fd_linear_modes(mutant=0):
     """FD shear-wave amplitude equals the exact linear prediction from the
     Fourier-space operator: symbol of D5 for each upwind direction, linearised
     BGK, and the RK3 polynomial G = I + dtL + (dtL)^2/2 + (dtL)^3/6 (eps huge so
-    the WENO weights are the linear ones)."""
+    the WENO weights are the linear ones), for the 3-, 4- and 5-node sets."""
     U = 1e-4
-    for n in (4, 5):
+    for n in (3, 4, 5):
         K = n * n
-        s6, s10 = math.sqrt(6), math.sqrt(10)
-        nodes = {4: [-math.sqrt(3 + s6), -math.sqrt(3 - s6), math.sqrt(3 - s6), math.sqrt(3 + s6)],
+        s3, s6, s10 = math.sqrt(3), math.sqrt(6), math.sqrt(10)
+        nodes = {3: [-s3, 0.0, s3],
+                 4: [-math.sqrt(3 + s6), -math.sqrt(3 - s6), math.sqrt(3 - s6), math.sqrt(3 + s6)],
                  5: [-math.sqrt(5 + s10), -math.sqrt(5 - s10), 0.0, math.sqrt(5 - s10), math.sqrt(5 + s10)]}[n]
-        w1 = {4: [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12],
+        w1 = {3: [1 / 6, 2 / 3, 1 / 6],
+              4: [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12],
               5: [(7 - 2 * s10) / 60, (7 + 2 * s10) / 60, 8 / 15, (7 + 2 * s10) / 60, (7 - 2 * s10) / 60]}[n]
         vx = np.tile(nodes, n)
         vy = np.repeat(nodes, n)
