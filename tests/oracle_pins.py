@@ -582,25 +582,31 @@ def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
 
 def check_fd_high_precision(mutant=0):
     """The oracle's FD step against a 30-digit mpmath brute force written from
-    the definitions (16 velocities with the closed-form Gauss-Hermite nodes
-    +-sqrt(3 -+ sqrt 6), weights (3 +- sqrt 6)/12; 6x6 lattice, 2 steps; a
-    rough state so that the nonlinear WENO weights are far from linear)."""
+    the definitions: 16 velocities with the closed-form Gauss-Hermite nodes
+    +-sqrt(3 -+ sqrt 6), weights (3 +- sqrt 6)/12 (2 steps), and 25 velocities
+    with nodes 0, +-sqrt(5 -+ sqrt 10), weights 8/15, (7 +- 2 sqrt 10)/60 (one
+    step; its zero components do not advect); 6x6 lattice, a rough state so
+    that the nonlinear WENO weights are far from linear."""
     import mpmath as mp
     mp.mp.dps = 30
-    s6 = mp.sqrt(6)
-    nodes = [-mp.sqrt(3 + s6), -mp.sqrt(3 - s6), mp.sqrt(3 - s6), mp.sqrt(3 + s6)]
-    weights = [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12]
+    s6, s10 = mp.sqrt(6), mp.sqrt(10)
+    sets = {4: ([-mp.sqrt(3 + s6), -mp.sqrt(3 - s6), mp.sqrt(3 - s6), mp.sqrt(3 + s6)],
+                [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12], 2),
+            5: ([-mp.sqrt(5 + s10), -mp.sqrt(5 - s10), mp.mpf(0), mp.sqrt(5 - s10), mp.sqrt(5 + s10)],
+                [(7 - 2 * s10) / 60, (7 + 2 * s10) / 60, mp.mpf(8) / 15, (7 + 2 * s10) / 60, (7 - 2 * s10) / 60], 1)}
     nx = ny = 6
-    rho, ux, uy = wl.random_smooth(nx, ny, seed=31, amp_rho=0.2, amp_u=0.1)
-    f0 = oracle.equilibrium(4, rho, ux, uy, mutant)
-    f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=32, lo=-0.2, hi=0.2))
-    dx, dt, tau, eps = 1.0 / nx, 0.02, 0.05, 1e-6
-    fm = [[[mp.mpf(float(f0[k, y, x])) for x in range(nx)] for y in range(ny)] for k in range(16)]
-    fm = _fd_mp_run(fm, nodes, weights, mp.mpf(dx), mp.mpf(dt), mp.mpf(tau), mp.mpf(eps), 2, mp)
-    exact = np.array([[[float(fm[k][y][x]) for x in range(nx)] for y in range(ny)] for k in range(16)])
-    fo = oracle.fd_run(f0, dx, dt, tau, 2, eps=eps, mutant=mutant)
-    err = np.max(np.abs(fo - exact)) / np.max(np.abs(exact))
-    assert err < 1e-13, err
+    for n, (nodes, weights, steps) in sets.items():
+        K = n * n
+        rho, ux, uy = wl.random_smooth(nx, ny, seed=31, amp_rho=0.2, amp_u=0.1)
+        f0 = oracle.equilibrium(n, rho, ux, uy, mutant)
+        f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=32, lo=-0.2, hi=0.2))
+        dx, dt, tau, eps = 1.0 / nx, 0.02, 0.05, 1e-6
+        fm = [[[mp.mpf(float(f0[k, y, x])) for x in range(nx)] for y in range(ny)] for k in range(K)]
+        fm = _fd_mp_run(fm, nodes, weights, mp.mpf(dx), mp.mpf(dt), mp.mpf(tau), mp.mpf(eps), steps, mp)
+        exact = np.array([[[float(fm[k][y][x]) for x in range(nx)] for y in range(ny)] for k in range(K)])
+        fo = oracle.fd_run(f0, dx, dt, tau, steps, eps=eps, mutant=mutant)
+        err = np.max(np.abs(fo - exact)) / np.max(np.abs(exact))
+        assert err < 1e-13, (n, err)
 
 
 def check_fd_decay_closed_form(mutant=0):
