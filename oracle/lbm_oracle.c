@@ -301,13 +301,21 @@ static double face_value(const double* g, int n, int64_t st, int i, double v, do
 
 /* Right-hand side L(f) of the semi-discrete FD equation. Lf has f's shape.
  * Moments (and so f^eq) are taken from the f passed in. */
+#if OR_MUTANT == 9
+static const double* mutant_fn = 0; /* planted: the BGK moments of every stage taken from f^n */
+#endif
+
 void or_fd_rhs(int nx, int ny, int K, const double* vx, const double* vy, const double* w,
                double dx, double tau, double eps, const double* f, double* Lf) {
     int64_t plane = (int64_t)nx * ny;
     double* rho = (double*)malloc(sizeof(double) * plane * 3);
     double* ux = rho + plane;
     double* uy = ux + plane;
+#if OR_MUTANT == 9
+    or_macro(nx, ny, K, vx, vy, mutant_fn ? mutant_fn : f, rho, ux, uy); /* planted */
+#else
     or_macro(nx, ny, K, vx, vy, f, rho, ux, uy);
+#endif
     for (int k = 0; k < K; ++k) {
         const double* g = f + k * plane;
         for (int y = 0; y < ny; ++y)
@@ -344,6 +352,9 @@ void or_fd_step(int nx, int ny, int K, const double* vx, const double* vy, const
     double* L = work;
     double* f1 = work + n;
     double* f2 = work + 2 * n;
+#if OR_MUTANT == 9
+    mutant_fn = f; /* planted; f is not overwritten before the third stage's L */
+#endif
     or_fd_rhs(nx, ny, K, vx, vy, w, dx, tau, eps, f, L);
     for (int64_t i = 0; i < n; ++i) f1[i] = f[i] + dt * L[i];
     or_fd_rhs(nx, ny, K, vx, vy, w, dx, tau, eps, f1, L);
@@ -353,6 +364,9 @@ void or_fd_step(int nx, int ny, int K, const double* vx, const double* vy, const
     for (int64_t i = 0; i < n; ++i) f2[i] = 0.75 * f[i] + 0.25 * (f1[i] + dt * L[i]);
 #endif
     or_fd_rhs(nx, ny, K, vx, vy, w, dx, tau, eps, f2, L);
+#if OR_MUTANT == 9
+    mutant_fn = 0;
+#endif
     for (int64_t i = 0; i < n; ++i) f[i] = (1.0 / 3.0) * f[i] + (2.0 / 3.0) * (f2[i] + dt * L[i]);
 }
 

@@ -20,6 +20,8 @@ MUTANTS = {
     7: ("WENO: downwind stencil for v > 0", [P.check_fd_linear_advection, P.check_fd_linear_modes,
                                             P.check_fd_high_precision]),
     8: ("WENO: wrong beta_2 coefficient", [P.check_weno_beta, P.check_fd_high_precision]),
+    9: ("FD: BGK moments of every stage taken from f^n", [P.check_fd_high_precision, P.check_fd_linear_modes,
+                                                          P.check_fd_decay_closed_form]),
 }
 
 
