@@ -161,6 +161,25 @@ int lbm_create(lbm_ctx** out, int model, int q_per_axis, int nx, int ny, double 
 /* Same as lbm_create with the parameters in a struct. */
 int lbm_create_spec(lbm_ctx** out, const lbm_spec* spec, void* cuda_stream);
 
+/* Resolve a spec from a kinematic viscosity instead of a relaxation time
+ * (Sec. 3 unit mapping). in gives model, q_per_axis, nx, ny, precision,
+ * storage, dt, dx and rho0 with the meaning and defaults of lbm_create (its
+ * tau is ignored); nu > 0 is given in the units of model nu_model (LBM_CS:
+ * lattice units, LBM_FD: FD units). A viscosity in the other model's units
+ * is converted with nu_LU = N nu_FD (Sec. 3: nu_ref;LU = nu_ref;FD / N), N =
+ * n_ref nodes of the CS lattice along the reference length (0 selects nx).
+ * Then tau follows from the model's own relation: CS tau_LU = nu_LU + dt/2
+ * (Eq. nulu, so an FD viscosity gives tau_LU = N tau_FD + sqrt(3)/6 with the
+ * default dt, Eq. nu-transfer); FD tau_FD = nu_FD (Eq. nu_fd, T = m = 1).
+ * *out receives the resolved spec, validated as lbm_create validates it
+ * (same error codes). Host only: no device work. LBM_EINVAL for null
+ * pointers, nu not positive and finite, a bad nu_model or n_ref < 0. */
+int lbm_spec_from_nu(const lbm_spec* in, double nu, int nu_model, int n_ref, lbm_spec* out);
+
+/* lbm_create from a viscosity: lbm_spec_from_nu, then lbm_create_spec.
+ * Same errors as both; on error *out is NULL. */
+int lbm_create_nu(lbm_ctx** out, const lbm_spec* in, double nu, int nu_model, int n_ref, void* cuda_stream);
+
 /* Release all device memory of the context (after finishing its stream).
  * NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
@@ -421,10 +440,10 @@ int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds);
 
 /* ---- observables without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory: code issued while a stream is being
- * captured into a CUDA graph (cudaMalloc is not capturable), hosts that hand
- * out a fixed memory arena and forbid further allocation, and
- * latency-sensitive loops where cudaMalloc would synchronise the device.
+ * cannot allocate device memory: hosts that hand the library a fixed memory
+ * arena and forbid any further allocation (an embedding application that
+ * owns all device memory), and latency-sensitive loops where a cudaMalloc
+ * would synchronise the device and stall the work in flight.
  *
  * It computes what lbm_observables computes (float64 mass, momentum and
  * probe amplitude) for a state in caller-owned device memory, and allocates
@@ -434,9 +453,13 @@ int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds);
  * larger lattices are covered by fewer, longer-striding blocks.
  *
  *  state: device pointer; element (k, y, x) at state + k*plane + y*pitch + x,
- *      float64 full f (LBM_FP64) or float32 f - w_k rho0 (LBM_FP32_DEV). A CS
- *      state is in the storage phase lbm_device_view reports
- *      (f_k(x) = stored_k(x - c_k)); FD states are f itself.
+ *      float64 full f (LBM_FP64) or float32 f - w_k rho0 (LBM_FP32_DEV).
+ *  cs_phase: how the populations sit in state, the value lbm_device_view
+ *      reports in cs_pull_phase: 0 node order, f_k(x) = stored_k(x) (FD, and
+ *      in-place CS after an even number of steps); 1 pull form of two-buffer
+ *      CS, f_k(x) = stored_k(x - c_k); 2 in-place CS after an odd number of
+ *      steps, f_k(x) = stored_{8-k}(x - c_k). LBM_EINVAL outside 0..2, or
+ *      non-zero for FD.
  *  comp: -1 for no probe, else 0 (u_x) / 1 (u_y) with device tables px[nx],
  *      py[ny] and norm as in lbm_set_probe.
  *  step, dt: copied into the record (time = step * dt).
@@ -449,7 +472,7 @@ int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds);
  * reads, so calls do not depend on each other's leftovers, but calls that
  * overlap on the GPU (different streams, no ordering) race on the array. */
 int lbm_observables_noalloc(int model, int q_per_axis, int precision, int nx, int ny, const void* state,
-                            int64_t plane, int32_t pitch, double rho0, int comp, const double* px,
+                            int64_t plane, int32_t pitch, int32_t cs_phase, double rho0, int comp, const double* px,
                             const double* py, double norm, int64_t step, double dt, lbm_obs* out,
                             void* cuda_stream);
 

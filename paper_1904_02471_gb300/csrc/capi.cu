@@ -152,6 +152,47 @@ int lbm_create(lbm_ctx** out, int model, int q, int nx, int ny, double tau, doub
     return lbm_create_spec(out, &s, stream);
 }
 
+int lbm_spec_from_nu(const lbm_spec* in, double nu, int nu_model, int n_ref, lbm_spec* out) {
+    GUARD_BEGIN
+    if (!in || !out) {
+        lbm::set_error("lbm_spec_from_nu: null spec");
+        return LBM_EINVAL;
+    }
+    if (!(nu > 0) || !std::isfinite(nu) || (nu_model != LBM_CS && nu_model != LBM_FD) || n_ref < 0) {
+        lbm::set_error("lbm_spec_from_nu: nu must be positive and finite, nu_model LBM_CS or LBM_FD, n_ref >= 0");
+        return LBM_EINVAL;
+    }
+    lbm_spec s = *in;
+    const double n = n_ref > 0 ? (double)n_ref : (double)s.nx;
+    if (!(n >= 1)) {
+        lbm::set_error("lbm_spec_from_nu: the reference length needs at least one node");
+        return LBM_EINVAL;
+    }
+    // viscosity in the target model's own units (Sec. 3: nu_LU = N nu_FD)
+    double nu_m = nu;
+    if (nu_model != s.model) nu_m = s.model == LBM_CS ? n * nu : nu / n;
+    if (s.model == LBM_CS) {
+        double dt = s.dt;  // the defaults of lbm_create: dt = 1/sqrt(3), or dx/sqrt(3)
+        if (dt == 0) dt = s.dx == 0 ? 1.0 / kSqrt3 : s.dx / kSqrt3;
+        s.tau = nu_m + 0.5 * dt;  // Eq. (nulu)
+    } else {
+        s.tau = nu_m;             // Eq. (nu_fd), T = m = 1
+    }
+    return lbm::Engine::validate(&s, out);
+    GUARD_END
+}
+
+int lbm_create_nu(lbm_ctx** out, const lbm_spec* in, double nu, int nu_model, int n_ref, void* stream) {
+    GUARD_BEGIN
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    lbm_spec s;
+    const int rc = lbm_spec_from_nu(in, nu, nu_model, n_ref, &s);
+    if (rc != LBM_OK) return rc;
+    return lbm_create_spec(out, &s, stream);
+    GUARD_END
+}
+
 void lbm_destroy(lbm_ctx* c) {
     try {
         delete c;

@@ -12,25 +12,15 @@
 // addition on here, reduced block-wise into partials and then in a fixed
 // order by a single block (deterministic).
 #include "kernels.h"
+#include "obs.cuh"
 
 namespace lbm {
 
-template <int Q1>
-__device__ __forceinline__ int lat_c(int i) {
-    return Q1 == 3 ? c3_of(i) : 0;
-}
-
-// Where f_k(x) of a lattice is stored: buffer, shift by -c_k, mirrored plane.
-struct StoreMap {
-    int buf;
-    bool shift;
-    bool mirror;
-};
+// Buffer that holds a lattice's current state (two-buffer CS: the current
+// one of the pair; in-place CS and FD: buffer 0).
 template <bool PULL>
-__device__ __forceinline__ StoreMap store_map(const LatDesc* d) {
-    if (!PULL) return {0, false, false};               // FD: node order
-    if (!d->inplace) return {d->cur, true, false};     // two-buffer CS: pull form
-    return {0, d->cur != 0, d->cur != 0};              // in-place CS, by phase
+__device__ __forceinline__ int store_buf(const LatDesc* d) {
+    return PULL && !d->inplace ? d->cur : 0;
 }
 
 template <typename T, int Q1, bool PULL>
@@ -40,8 +30,8 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    const StoreMap m = store_map<PULL>(d);
-    T* __restrict__ out = static_cast<T*>(d->buf[m.buf]);
+    const StoreMap m = store_map_of_phase(desc_phase(d, PULL));
+    T* __restrict__ out = static_cast<T*>(d->buf[store_buf<PULL>(d)]);
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
@@ -57,14 +47,7 @@ __global__ void init_eq_kernel(const LatDesc* d, int nx, int ny, const double* _
             const T xi = (T)vx_of<Q1>(k) * u + (T)vy_of<Q1>(k) * v;
             // Eq. (herfeq) minus the storage offset w_k rho0
             const T dev = (T)w_of<Q1>(k) * (dr + r * (xi + T(0.5) * (xi * xi - usq)));
-            int xd = x, yd = y;
-            if (m.shift) {
-                xd = x - lat_c<Q1>(k % Q1);
-                yd = y - lat_c<Q1>(k / Q1);
-                xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
-            }
-            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd;
+            const long long off = stored_offset<Q1>(m, k, x, y, nx, ny, plane, pitch);
             if (LBM_BC_NODE(d, K, off)) out[off] = (T)dev;
         }
     }
@@ -76,21 +59,14 @@ __global__ void set_pop_kernel(const LatDesc* d, int nx, int ny, const double* _
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    const StoreMap m = store_map<PULL>(d);
-    T* __restrict__ out = static_cast<T*>(d->buf[m.buf]);
+    const StoreMap m = store_map_of_phase(desc_phase(d, PULL));
+    T* __restrict__ out = static_cast<T*>(d->buf[store_buf<PULL>(d)]);
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            int xd = x, yd = y;
-            if (m.shift) {
-                xd = x - lat_c<Q1>(k % Q1);
-                yd = y - lat_c<Q1>(k / Q1);
-                xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
-            }
-            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)yd * pitch + xd;
+            const long long off = stored_offset<Q1>(m, k, x, y, nx, ny, plane, pitch);
             const double fv = f[k * n + c];
             if (!isfinite(fv)) atomicOr(d->err, ERR_INPUT);
             if (LBM_BC_NODE(d, K, off)) out[off] = (T)(fv - w_of<Q1>(k) * r0);
@@ -110,8 +86,8 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const double r0 = d->rho0;
-    const StoreMap m = store_map<PULL>(d);
-    const T* __restrict__ in = static_cast<const T*>(d->buf[m.buf]);
+    const StoreMap m = store_map_of_phase(desc_phase(d, PULL));
+    const T* __restrict__ in = static_cast<const T*>(d->buf[store_buf<PULL>(d)]);
     const int pc = d->probe_comp;
     const long long n = (long long)wx * wy;
     double acc[NOBS] = {0.0, 0.0, 0.0, 0.0};
@@ -122,14 +98,7 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
         double dr = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            int xs = x, ys = y;
-            if (m.shift) {
-                xs = x - lat_c<Q1>(k % Q1);
-                ys = y - lat_c<Q1>(k / Q1);
-                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-                ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-            }
-            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs;
+            const long long off = stored_offset<Q1>(m, k, x, y, nx, ny, plane, pitch);
             const double s = LBM_BC_NODE(d, K, off) ? (double)in[off] : 0.0;
             if (f) f[k * n + c] = s + w_of<Q1>(k) * r0;
             dr += s;
@@ -162,53 +131,22 @@ __global__ void __launch_bounds__(IO_THREADS) obs_snapshot_kernel(const LatDesc*
     const long long plane = d->plane;
     const int pitch = d->pitch;
     const T r0 = (T)d->rho0;
-    const StoreMap m = store_map<PULL>(d);
-    const T* __restrict__ in = static_cast<const T*>(d->buf[m.buf]);
+    const StoreMap m = store_map_of_phase(desc_phase(d, PULL));
+    const T* __restrict__ in = static_cast<const T*>(d->buf[store_buf<PULL>(d)]);
     const int pc = d->probe_comp;
     const long long n = (long long)nx * ny;
     double acc[NOBS] = {0.0, 0.0, 0.0, 0.0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
-        T dr = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            int xs = x, ys = y;
-            if (m.shift) {
-                xs = x - lat_c<Q1>(k % Q1);
-                ys = y - lat_c<Q1>(k / Q1);
-                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-                ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-            }
-            const long long off = (m.mirror ? K - 1 - k : k) * plane + (long long)ys * pitch + xs;
-            const T s = LBM_BC_NODE(d, K, off) ? in[off] : T(0);
-            dr += s;
-            if (vx_of<Q1>(k) != 0.0) jx += s * (T)vx_of<Q1>(k);
-            if (vy_of<Q1>(k) != 0.0) jy += s * (T)vy_of<Q1>(k);
-        }
+        T dr, jx, jy;
+        stored_node_moments<T, Q1>(in, m, x, y, nx, ny, plane, pitch, dr, jx, jy,
+                                   [&](long long off) { return LBM_BC_NODE(d, K, off); });
         acc[0] += (double)dr;
         acc[1] += (double)jx;
         acc[2] += (double)jy;
         if (pc >= 0) acc[3] += (double)((pc == 0 ? jx : jy) / (r0 + dr)) * d->probe_px[x] * d->probe_py[y];
     }
     block_reduce_obs<double, IO_THREADS>(acc, part + (long long)blockIdx.x * NOBS, red);
-}
-
-// Deterministic block sum of n rows of NOBS doubles.
-__device__ void sum_rows(const double* __restrict__ p, long long n, double* out, double* sm) {
-    double a[NOBS] = {0.0, 0.0, 0.0, 0.0};
-    for (long long i = threadIdx.x; i < n; i += blockDim.x)
-#pragma unroll
-        for (int q = 0; q < NOBS; ++q) a[q] += p[i * NOBS + q];
-#pragma unroll
-    for (int q = 0; q < NOBS; ++q) sm[threadIdx.x * NOBS + q] = a[q];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int q = 0; q < NOBS; ++q) sm[threadIdx.x * NOBS + q] += sm[(threadIdx.x + s) * NOBS + q];
-        __syncthreads();
-    }
-    if (threadIdx.x < NOBS) out[threadIdx.x] = sm[threadIdx.x];
 }
 
 constexpr int FIN_THREADS = 256;
@@ -222,17 +160,8 @@ __global__ void __launch_bounds__(FIN_THREADS) snap_finalize_kernel(LatDesc* d, 
 }
 
 __device__ void write_record(LatDesc* d, long long step, const double* tot) {
-    const double n = (double)d->nx * (double)d->ny;
-    lbm_obs o;
-    o.step = step;
-    o.time = (double)step * d->dt;
-    o.mass = n * d->rho0 + tot[0];
-    o.mom_x = tot[1];
-    o.mom_y = tot[2];
-    o.amp = d->probe_comp >= 0 ? d->probe_norm * tot[3] : 0.0;
-    o.nonfinite = (isfinite(o.mass) && isfinite(o.amp) && isfinite(o.mom_x) && isfinite(o.mom_y)) ? 0 : 1;
-    o.reserved = 0;
-    d->series[(step - d->obs_base) / d->obs_every] = o;
+    d->series[(step - d->obs_base) / d->obs_every] =
+        make_obs(step, d->dt, d->nx, d->ny, d->rho0, d->probe_comp, d->probe_norm, tot);
 }
 
 // Two-level reduction of the tile partials of every lattice observing at

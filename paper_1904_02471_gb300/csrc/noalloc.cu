@@ -1,9 +1,9 @@
 // Allocation-free observables of a lattice state held in caller memory.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation),
-// hosts that hand the library a fixed arena and forbid further allocation,
-// and latency-sensitive loops where cudaMalloc would synchronise the device.
+// Some callers cannot call cudaMalloc: hosts that hand the library a fixed
+// arena and forbid further allocation (an embedding application that owns
+// all device memory), and latency-sensitive loops where cudaMalloc would
+// synchronise the device and stall the work in flight.
 // For them this file offers lbm_observables_noalloc: the same float64
 // reduction as lbm_observables, but its block partial sums live in a
 // file-scope device array (NOALLOC_MAX_BLOCKS x 4 doubles = 32 KiB) that
@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "engine.h"
+#include "obs.cuh"
 
 namespace lbm {
 namespace {
@@ -30,6 +31,7 @@ struct NoallocArgs {
     const void* state;
     long long plane;
     int pitch, nx, ny;
+    int phase;   // storage phase of a CS state (lbm_view::cs_pull_phase); 0 for FD
     double rho0;
     int comp;
     const double* px;
@@ -39,37 +41,21 @@ struct NoallocArgs {
     double dt;
 };
 
-template <int Q1>
-__device__ __forceinline__ int noalloc_c(int i) {
-    return Q1 == 3 ? c3_of(i) : 0;
-}
-
-template <typename T, int Q1, bool PULL>
+// Per-node moments read through the state's storage phase (the helpers the
+// library's own observables snapshot uses), then float64 block partials.
+template <typename T, int Q1>
 __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_partials_kernel(NoallocArgs a, double* part) {
-    constexpr int K = Q1 * Q1;
     __shared__ double red[(NOALLOC_THREADS / 32) * NOBS];
     const T* in = static_cast<const T*>(a.state);
+    const StoreMap m = store_map_of_phase(a.phase);
     const long long n = (long long)a.nx * a.ny;
     double acc[NOBS] = {0.0, 0.0, 0.0, 0.0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % a.nx), y = (int)(c / a.nx);
-        // per node in the storage precision, then float64 (as lbm_observables)
-        T dr = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            int xs = x, ys = y;
-            if (PULL) {  // CS storage phase: f_k(x) = stored_k(x - c_k)
-                xs = x - noalloc_c<Q1>(k % Q1);
-                ys = y - noalloc_c<Q1>(k / Q1);
-                xs = xs < 0 ? xs + a.nx : (xs >= a.nx ? xs - a.nx : xs);
-                ys = ys < 0 ? ys + a.ny : (ys >= a.ny ? ys - a.ny : ys);
-            }
-            const T s = in[k * a.plane + (long long)ys * a.pitch + xs];
-            dr += s;
-            if (vx_of<Q1>(k) != 0.0) jx += s * (T)vx_of<Q1>(k);
-            if (vy_of<Q1>(k) != 0.0) jy += s * (T)vy_of<Q1>(k);
-        }
+        T dr, jx, jy;
+        stored_node_moments<T, Q1>(in, m, x, y, a.nx, a.ny, a.plane, a.pitch, dr, jx, jy,
+                                   [](long long) { return true; });
         acc[0] += (double)dr;
         acc[1] += (double)jx;
         acc[2] += (double)jy;
@@ -81,31 +67,10 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_partials_kernel(Noall
 __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_finalize_kernel(NoallocArgs a, const double* part,
                                                                           int nblocks, lbm_obs* out) {
     __shared__ double sm[NOALLOC_THREADS * NOBS];
-    double v[NOBS] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x)
-#pragma unroll
-        for (int q = 0; q < NOBS; ++q) v[q] += part[i * NOBS + q];
-#pragma unroll
-    for (int q = 0; q < NOBS; ++q) sm[threadIdx.x * NOBS + q] = v[q];
+    __shared__ double tot[NOBS];
+    sum_rows(part, nblocks, tot, sm);
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int q = 0; q < NOBS; ++q) sm[threadIdx.x * NOBS + q] += sm[(threadIdx.x + s) * NOBS + q];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        lbm_obs o;
-        o.step = a.step;
-        o.time = (double)a.step * a.dt;
-        o.mass = (double)a.nx * (double)a.ny * a.rho0 + sm[0];
-        o.mom_x = sm[1];
-        o.mom_y = sm[2];
-        o.amp = a.comp >= 0 ? a.norm * sm[3] : 0.0;
-        o.nonfinite = (isfinite(o.mass) && isfinite(o.amp) && isfinite(o.mom_x) && isfinite(o.mom_y)) ? 0 : 1;
-        o.reserved = 0;
-        *out = o;
-    }
+    if (threadIdx.x == 0) *out = make_obs(a.step, a.dt, a.nx, a.ny, a.rho0, a.comp, a.norm, tot);
 }
 
 // Looks up (once per device, with that device current) the device address
@@ -133,7 +98,7 @@ int noalloc_scratch(double** out) {
 }  // namespace lbm
 
 extern "C" int lbm_observables_noalloc(int model, int q_per_axis, int precision, int nx, int ny, const void* state,
-                                       int64_t plane, int32_t pitch, double rho0, int comp, const double* px,
+                                       int64_t plane, int32_t pitch, int32_t cs_phase, double rho0, int comp, const double* px,
                                        const double* py, double norm, int64_t step, double dt, lbm_obs* out,
                                        void* cuda_stream) {
     using namespace lbm;
@@ -148,6 +113,10 @@ extern "C" int lbm_observables_noalloc(int model, int q_per_axis, int precision,
             set_error("lbm_observables_noalloc: lattice size beyond the maximum (nx*ny < 2^31) or bad layout");
             return LBM_EINVAL;
         }
+        if (cs_phase < 0 || cs_phase > 2 || (model == LBM_FD && cs_phase != 0)) {
+            set_error("lbm_observables_noalloc: cs_phase must be 0, 1 or 2 for CS and 0 for FD");
+            return LBM_EINVAL;
+        }
         if (comp >= 0 && (comp > 1 || !px || !py)) {
             set_error("lbm_observables_noalloc: probe needs comp 0/1 and device tables px, py");
             return LBM_EINVAL;
@@ -155,23 +124,20 @@ extern "C" int lbm_observables_noalloc(int model, int q_per_axis, int precision,
         double* part = nullptr;
         int rc = noalloc_scratch(&part);
         if (rc != LBM_OK) return rc;
-        NoallocArgs a{state, (long long)plane, pitch, nx, ny, precision == LBM_FP64 ? 0.0 : rho0,
+        NoallocArgs a{state, (long long)plane, pitch, nx, ny, cs_phase, precision == LBM_FP64 ? 0.0 : rho0,
                       comp >= 0 ? comp : -1, px, py, norm, (long long)step, dt};
         const long long n = (long long)nx * ny;
         long long nb = (n + NOALLOC_THREADS - 1) / NOALLOC_THREADS;
         const int grid = (int)(nb < NOALLOC_MAX_BLOCKS ? nb : NOALLOC_MAX_BLOCKS);
         cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-        const bool pull = model == LBM_CS;
         if (precision == LBM_FP64) {
-            if (pull) noalloc_partials_kernel<double, 3, true><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else if (q_per_axis == 3) noalloc_partials_kernel<double, 3, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else if (q_per_axis == 4) noalloc_partials_kernel<double, 4, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else noalloc_partials_kernel<double, 5, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            if (q_per_axis == 3) noalloc_partials_kernel<double, 3><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            else if (q_per_axis == 4) noalloc_partials_kernel<double, 4><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            else noalloc_partials_kernel<double, 5><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
         } else {
-            if (pull) noalloc_partials_kernel<float, 3, true><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else if (q_per_axis == 3) noalloc_partials_kernel<float, 3, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else if (q_per_axis == 4) noalloc_partials_kernel<float, 4, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
-            else noalloc_partials_kernel<float, 5, false><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            if (q_per_axis == 3) noalloc_partials_kernel<float, 3><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            else if (q_per_axis == 4) noalloc_partials_kernel<float, 4><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
+            else noalloc_partials_kernel<float, 5><<<grid, NOALLOC_THREADS, 0, s>>>(a, part);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "noalloc_partials_kernel");

@@ -91,6 +91,8 @@ _SIGS = [
     ("lbm_fit_decay", _i, [_D, _D, _i64, _d, _D, _D]),
     ("lbm_create", _i, [ctypes.POINTER(_P), _i, _i, _i, _i, _d, _d, _d, _i, _d, _P]),
     ("lbm_create_spec", _i, [ctypes.POINTER(_P), ctypes.POINTER(lbm_spec), _P]),
+    ("lbm_spec_from_nu", _i, [ctypes.POINTER(lbm_spec), _d, _i, _i, ctypes.POINTER(lbm_spec)]),
+    ("lbm_create_nu", _i, [ctypes.POINTER(_P), ctypes.POINTER(lbm_spec), _d, _i, _i, _P]),
     ("lbm_destroy", None, [_P]),
     ("lbm_get_spec", _i, [_P, ctypes.POINTER(lbm_spec)]),
     ("lbm_set_weno_eps", _i, [_P, _d]),
@@ -146,8 +148,8 @@ _SIGS = [
                               ctypes.POINTER(_sz)]),
     ("lbm_server_destroy", None, [_P]),
     ("lbm_server_plan_round", _i, [ctypes.POINTER(lbm_spec), ctypes.POINTER(_i64), _i, _i, ctypes.POINTER(_i64)]),
-    ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, _d, _i, _P, _P, _d, _i64, _d,
-                                     _P, _P]),
+    ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, ctypes.c_int32, _d, _i, _P, _P,
+                                     _d, _i64, _d, _P, _P]),
 ]
 
 
@@ -260,13 +262,33 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
-class Lattice:
-    """One lattice context (lbm_create ... lbm_destroy)."""
+def spec_from_nu(model, q, nx, ny, nu, nu_model=None, n_ref=0, dt=0.0, dx=0.0, precision="fp64", rho0=0.0,
+                 storage="ab") -> lbm_spec:
+    """lbm_spec_from_nu: the resolved spec of a lattice given its viscosity
+    (in the units of nu_model, default the lattice's own model)."""
+    s = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage)
+    nm = s.model if nu_model is None else (MODELS[nu_model] if isinstance(nu_model, str) else nu_model)
+    out = lbm_spec()
+    check(lib().lbm_spec_from_nu(ctypes.byref(s), nu, nm, n_ref, ctypes.byref(out)), "lbm_spec_from_nu")
+    return out
 
-    def __init__(self, model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, stream=None, storage="ab"):
+
+class Lattice:
+    """One lattice context (lbm_create ... lbm_destroy). With nu given instead
+    of tau (tau=None) the context is made by lbm_create_nu."""
+
+    def __init__(self, model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, stream=None, storage="ab",
+                 nu=None, nu_model=None, n_ref=0):
         self._h = ctypes.c_void_p()
-        spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0, storage)
-        check(lib().lbm_create_spec(ctypes.byref(self._h), ctypes.byref(spec), _stream_ptr(stream)), "lbm_create")
+        if tau is None:
+            spec = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage)
+            nm = spec.model if nu_model is None else (MODELS[nu_model] if isinstance(nu_model, str) else nu_model)
+            check(lib().lbm_create_nu(ctypes.byref(self._h), ctypes.byref(spec), nu, nm, n_ref,
+                                      _stream_ptr(stream)), "lbm_create_nu")
+        else:
+            spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0, storage)
+            check(lib().lbm_create_spec(ctypes.byref(self._h), ctypes.byref(spec), _stream_ptr(stream)),
+                  "lbm_create")
         out = lbm_spec()
         check(lib().lbm_get_spec(self._h, ctypes.byref(out)), "lbm_get_spec")
         self.spec = out

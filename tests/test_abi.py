@@ -189,3 +189,49 @@ def test_server_round_plan():
     with pytest.raises(lbm.LbmError) as e:                                      # a bad spec as in lbm_create
         lbm.plan_round([pkg.make_spec("cs", 4, 64, 64, 0.6, 0.0, 0.0, "fp32")], [10], 8)
     assert e.value.code == lbm.LBM_EINVAL
+
+
+def test_spec_from_nu_against_printed_tau_lu():
+    """lbm_spec_from_nu (Sec. 3): a CS lattice from the FD viscosity
+    nu_FD = 5e-4 (or from nu_LU = 5e-4 N in its own units) gets the tau_LU
+    column of Tables 1-2; an FD lattice from either gets tau_FD = 5e-4."""
+    g = P._golden("paper_values.json")
+    t = g["tau_lu_tables"]
+    nu_fd = t["tau_fd"]
+    for n, printed in t["rows"]:
+        for nu, units in ((nu_fd, "fd"), (nu_fd * n, "cs")):
+            s = pkg.spec_from_nu("cs", 3, n, 1, nu, units)
+            assert P._trunc(s.tau, t["digits"]) == printed
+            assert abs(s.tau - pkg.lbm_tau_lu_from_fd(n, nu_fd)) < 1e-15
+            assert abs(s.dt - 1 / math.sqrt(3)) < 1e-16 and s.dx == 1.0
+            f = pkg.spec_from_nu("fd", 4, n, n, nu, units, dt=nu_fd)
+            assert abs(f.tau - nu_fd) < 1e-18 and abs(f.dx - 1.0 / n) < 1e-18
+    # the shock-tube pair of Sec. 4.1 (N = 2048), with the reference length
+    # given apart from the lattice width
+    s = g["tau_lu_shock"]
+    for tau_fd, printed, digits in s["rows"]:
+        c = pkg.spec_from_nu("cs", 3, 2048, 4, tau_fd, "fd", n_ref=s["n"])
+        assert P._trunc(c.tau, digits) == printed
+    # a CS dt other than the default enters through Eq. (nulu)
+    c = pkg.spec_from_nu("cs", 3, 16, 16, 0.1, "cs", dt=0.5, dx=0.5 * math.sqrt(3))
+    assert abs(c.tau - 0.35) < 1e-15
+
+
+@pytest.mark.parametrize("args,code", [
+    (dict(model="cs", q=3, nx=8, ny=8, nu=0.0), lbm.LBM_EINVAL),           # nu must be positive
+    (dict(model="cs", q=3, nx=8, ny=8, nu=float("nan")), lbm.LBM_EINVAL),
+    (dict(model="cs", q=3, nx=8, ny=8, nu=0.1, nu_model=7), lbm.LBM_EINVAL),
+    (dict(model="cs", q=3, nx=8, ny=8, nu=0.1, n_ref=-1), lbm.LBM_EINVAL),
+    (dict(model="fd", q=4, nx=32, ny=32, nu=1e-4, dt=1e-3), lbm.LBM_ESTIFF),  # dt > tau_FD = nu
+    (dict(model="fd", q=4, nx=32, ny=32, nu=1e-2, dt=1.5e-2), lbm.LBM_ECFL),
+])
+def test_spec_from_nu_validation(args, code):
+    a = dict(args)
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.spec_from_nu(a.pop("model"), a.pop("q"), a.pop("nx"), a.pop("ny"), a.pop("nu"), **a)
+    assert ei.value.code == code
+    # lbm_create_nu refuses the same before any device work
+    a = dict(args)
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Lattice(a.pop("model"), a.pop("q"), a.pop("nx"), a.pop("ny"), None, **a)
+    assert ei.value.code == code
