@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(IO_THREADS) readout_kernel(const LatDesc* d, i
 template <typename T, int Q1, bool PULL>
 __global__ void __launch_bounds__(IO_THREADS) obs_snapshot_kernel(const LatDesc* d, int nx, int ny,
                                                                   double* __restrict__ part) {
-    constexpr int K = Q1 * Q1;
+    [[maybe_unused]] constexpr int K = Q1 * Q1;   // used by the bounds-checked build
     __shared__ double red[(IO_THREADS / 32) * NOBS];
     const long long plane = d->plane;
     const int pitch = d->pitch;

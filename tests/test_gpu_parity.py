@@ -99,6 +99,68 @@ def test_fd_fp64_taylor_green_q4_1000_steps():
     assert rel_err(f, ref) < TOL64
 
 
+def _fd_interior_tiles(nx, ny, tx=32, ty=8):
+    """Tiles whose staged halo (4 columns, 3 rows) needs no periodic wrap:
+    the kernel stages those along its interior path."""
+    return [(x0, y0) for x0 in range(0, nx, tx) for y0 in range(0, ny, ty)
+            if x0 >= 4 and x0 + tx + 4 <= nx and y0 >= 3 and y0 + ty + 3 <= ny]
+
+
+@pytest.mark.parametrize("q", [4, 5])
+def test_fd_fp64_interior_tiles_1000_steps(q):
+    """1000 FD steps on a lattice with interior 32 x 8 tiles (staged without
+    wrap) and edge tiles, from a rough state, against the oracle at 1e-12 in
+    every population. The oracle runs in a thread beside the GPU run (ctypes
+    releases the interpreter lock)."""
+    import concurrent.futures as cf
+    nx, ny = 72, 44
+    assert len(_fd_interior_tiles(nx, ny)) == 4
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=50 + q, amp_rho=0.05, amp_u=0.05)
+    f0 = oracle.equilibrium(q, rho, ux, uy)
+    f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=11 + q, lo=-0.01, hi=0.01))
+    dx = 1.0 / nx
+    vmax = {4: 2.3344142183389773, 5: 2.8569700138728056}[q]
+    dt = 0.4 * dx / vmax
+    tau = 1.5 * dt
+    with cf.ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle.fd_run, f0, dx, dt, tau, 1000)
+        with pkg.Lattice("fd", q, nx, ny, tau, dt=dt) as L:
+            L.config(0, 0)   # 32 x 8 tiles, one block per tile
+            L.set_populations(f0)
+            L.step(1000)
+            f = L.populations()
+        ref = fut.result()
+    assert np.all(np.isfinite(ref))
+    assert rel_err(f, ref) < TOL64
+
+
+def test_create_from_viscosity_equals_create_from_tau():
+    """lbm_create_nu (Sec. 3): a CS lattice made from nu_FD with N = nx has
+    the tau_LU of Eq. (nu-transfer) (to rounding: tau = N nu + dt/2 and
+    N tau + sqrt(3)/6 may differ in the last bit), an FD lattice made from
+    nu_LU = N nu_FD has tau_FD = nu_FD, and each computes bit-identically
+    what the lattice made from its resolved spec computes."""
+    n = 40
+    nu_fd = 5e-4
+    rho, ux, uy = wl.shear_wave(n, 4, 0.01 * SQ3)
+    with pkg.Lattice("cs", 3, n, 4, None, nu=nu_fd, nu_model="fd") as A:
+        assert abs(A.spec.tau - pkg.lbm_tau_lu_from_fd(n, nu_fd)) < 1e-15
+        B = pkg.Lattice("cs", 3, n, 4, A.spec.tau)
+        for L in (A, B):
+            L.init(rho, ux, uy)
+            L.step(25)
+        assert np.array_equal(A.populations(), B.populations())
+        B.close()
+    rho, ux, uy = wl.shear_wave(n, n, 0.01)
+    with pkg.Lattice("fd", 4, n, n, None, dt=nu_fd, nu=nu_fd * n, nu_model="cs") as A, \
+            pkg.Lattice("fd", 4, n, n, nu_fd, dt=nu_fd) as B:
+        assert abs(A.spec.tau - nu_fd) < 1e-18
+        for L in (A, B):
+            L.init(rho, ux, uy)
+            L.step(5)
+        assert np.array_equal(A.populations(), B.populations())
+
+
 @pytest.mark.parametrize("q,nx,ny", [(3, 20, 18), (5, 20, 18), (4, 33, 9), (4, 1, 1), (4, 2, 5), (5, 3, 1)])
 def test_fd_fp64_random_state(q, nx, ny):
     rho, ux, uy = wl.random_smooth(nx, ny, seed=q * 100 + nx, amp_rho=0.1, amp_u=0.1)
