@@ -54,6 +54,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
         lib.or_fd_rhs.argtypes = [i, i, i, _D, _D, _D, d, d, d, _D, _D]
         lib.or_fd_step.argtypes = [i, i, i, _D, _D, _D, d, d, d, d, _D, _D]
         lib.or_fd_run.argtypes = [i, i, i, _D, _D, _D, d, d, d, d, i64, _D, _D]
+        lib.or_fd_imex_step.argtypes = [i, i, i, _D, _D, _D, d, d, d, d, _D, _D, _D]
+        lib.or_fd_imex_run.argtypes = [i, i, i, _D, _D, _D, d, d, d, d, i64, _D, _D]
         lib.or_observables.argtypes = [i, i, i, _D, _D, _D, i, _D, _D, d, _D]
         _LIBS[mutant] = lib
     return _LIBS[mutant]
@@ -197,6 +199,31 @@ def fd_run(f, dx: float, dt: float, tau: float, steps: int, eps: float = WENO_EP
     work = np.empty((3,) + f.shape)
     _lib(mutant).or_fd_run(nx, ny, K, _p(vx), _p(vy), _p(w), dx, dt, tau, eps, int(steps), _p(f), _p(work))
     return f
+
+
+def fd_imex_run(f, dx: float, dt: float, tau: float, steps: int, eps: float = WENO_EPS,
+                mutant: int = 0) -> np.ndarray:
+    """`steps` IMEX-SSP2(2,2,2) steps of f[k, y, x] (explicit WENO-5 advection,
+    implicit BGK; lifts dt < tau, Sec. 4.1)."""
+    f = _f64(f).copy()
+    K, ny, nx = f.shape
+    n = int(round(math.sqrt(K)))
+    vx, vy, w = velocity_set(n, mutant)
+    work = np.empty((7,) + f.shape)
+    _lib(mutant).or_fd_imex_run(nx, ny, K, _p(vx), _p(vy), _p(w), dx, dt, tau, eps, int(steps), _p(f), _p(work))
+    return f
+
+
+def fd_imex_stages(f, dx: float, dt: float, tau: float, eps: float = WENO_EPS, mutant: int = 0):
+    """One IMEX step: returns (f^{n+1}, [Y_1, Y_2]) with the stage values."""
+    f = _f64(f).copy()
+    K, ny, nx = f.shape
+    n = int(round(math.sqrt(K)))
+    vx, vy, w = velocity_set(n, mutant)
+    work = np.empty((7,) + f.shape)
+    ys = np.empty((2,) + f.shape)
+    _lib(mutant).or_fd_imex_step(nx, ny, K, _p(vx), _p(vy), _p(w), dx, dt, tau, eps, _p(f), _p(work), _p(ys))
+    return f, [ys[0], ys[1]]
 
 
 # --------------------------------------------------------------------------

@@ -376,6 +376,117 @@ void or_fd_run(int nx, int ny, int K, const double* vx, const double* vy, const 
 }
 
 /* ------------------------------------------------------------------------ */
+/* FD with an implicit-explicit (IMEX) Runge-Kutta step. Sec. 4.1 notes that  */
+/* the restriction dt < tau of the explicit scheme can be lifted with IMEX    */
+/* schemes and cites one without printing it. The scheme here is the          */
+/* second-order IMEX-SSP2(2,2,2) of Pareschi and Russo (J. Sci. Comput. 25,  */
+/* 2005): the advection A(f) = -v.grad f (WENO-5 flux differences, as in      */
+/* or_fd_rhs) is explicit, the BGK term C(f) = -(f - f^eq(f))/tau implicit,   */
+/* with the tableaux                                                          */
+/*   explicit: a~21 = 1, all other a~ = 0,          b~ = (1/2, 1/2)           */
+/*   implicit: a11 = a22 = g, a21 = 1 - 2g, a12 = 0, b = (1/2, 1/2)           */
+/*   g = 1 - 1/sqrt(2).                                                       */
+/* Stage i: Y_i = f^n + dt sum_{j<i} (a~_ij A(Y_j) + a_ij C(Y_j))             */
+/*               + dt a_ii C(Y_i),                                            */
+/* step:    f^{n+1} = f^n + dt sum_i (b~_i A(Y_i) + b_i C(Y_i)).              */
+/* The implicit equation of a stage is solved in closed form: C conserves     */
+/* rho and rho u, so Y_i has the moments of its explicit part Z_i (the first  */
+/* line), f^eq(Y_i) = f^eq(Z_i), and                                          */
+/*   Y_i = (Z_i + lam f^eq(Z_i)) / (1 + lam),   lam = dt a_ii / tau.          */
+/* C(Y_i) is then evaluated from Y_i's own moments, as the scheme states.     */
+/* ------------------------------------------------------------------------ */
+
+/* Advection part of L(f): A(f)_k = -v_kx dF_x/dx - v_ky dF_y/dx. */
+static void fd_advection(int nx, int ny, int K, const double* vx, const double* vy, double dx, double eps,
+                         const double* f, double* Af) {
+    int64_t plane = (int64_t)nx * ny;
+    for (int k = 0; k < K; ++k) {
+        const double* g = f + k * plane;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                double adv = 0.0;
+                if (vx[k] != 0.0) {
+                    const double* row = g + (int64_t)y * nx;
+                    adv = adv - vx[k] * (face_value(row, nx, 1, x, vx[k], eps) -
+                                         face_value(row, nx, 1, x - 1, vx[k], eps)) / dx;
+                }
+                if (vy[k] != 0.0) {
+                    const double* col = g + x;
+                    adv = adv - vy[k] * (face_value(col, ny, nx, y, vy[k], eps) -
+                                         face_value(col, ny, nx, y - 1, vy[k], eps)) / dx;
+                }
+                Af[k * plane + (int64_t)y * nx + x] = adv;
+            }
+    }
+}
+
+/* Collision part of L(f): C(f)_k = -(f_k - f^eq_k(f)) / tau, moments of f. */
+static void fd_collision(int nx, int ny, int K, const double* vx, const double* vy, const double* w, double tau,
+                         const double* f, double* Cf) {
+    int64_t plane = (int64_t)nx * ny;
+    for (int64_t c = 0; c < plane; ++c) {
+        double rho, ux, uy;
+        cell_moments(K, vx, vy, f + c, plane, &rho, &ux, &uy);
+        for (int k = 0; k < K; ++k)
+            Cf[k * plane + c] = -(f[k * plane + c] - feq_k(w[k], vx[k], vy[k], rho, ux, uy)) / tau;
+    }
+}
+
+/* One IMEX-SSP2(2,2,2) step. work holds 7 lattices; if ystages is not NULL
+ * it receives the two stage values Y_1, Y_2 (2 lattices). */
+void or_fd_imex_step(int nx, int ny, int K, const double* vx, const double* vy, const double* w,
+                     double dx, double dt, double tau, double eps, double* f, double* work, double* ystages) {
+    const int64_t plane = (int64_t)nx * ny, n = (int64_t)K * plane;
+#if OR_MUTANT == 11
+    const double g = 0.5; /* planted: gamma of the implicit tableau */
+#else
+    const double g = 1.0 - 1.0 / sqrt(2.0);
+#endif
+    const double ae[2][2] = {{0.0, 0.0}, {1.0, 0.0}};
+    const double ai[2][2] = {{g, 0.0}, {1.0 - 2.0 * g, g}};
+    const double be[2] = {0.5, 0.5}, bi[2] = {0.5, 0.5};
+    double* Y[2] = {work, work + n};
+    double* A[2] = {work + 2 * n, work + 3 * n};
+    double* C[2] = {work + 4 * n, work + 5 * n};
+    double* Z = work + 6 * n;
+    for (int i = 0; i < 2; ++i) {
+        /* explicit part of the stage */
+        for (int64_t m = 0; m < n; ++m) {
+            double z = f[m];
+            for (int j = 0; j < i; ++j) z = z + dt * (ae[i][j] * A[j][m] + ai[i][j] * C[j][m]);
+            Z[m] = z;
+        }
+        /* implicit part in closed form */
+        const double lam = dt * ai[i][i] / tau;
+        for (int64_t c = 0; c < plane; ++c) {
+            double rho, ux, uy;
+#if OR_MUTANT == 10
+            cell_moments(K, vx, vy, f + c, plane, &rho, &ux, &uy); /* planted: equilibrium of f^n */
+#else
+            cell_moments(K, vx, vy, Z + c, plane, &rho, &ux, &uy);
+#endif
+            for (int k = 0; k < K; ++k) {
+                const double fe = feq_k(w[k], vx[k], vy[k], rho, ux, uy);
+                Y[i][k * plane + c] = (Z[k * plane + c] + lam * fe) / (1.0 + lam);
+            }
+        }
+        fd_advection(nx, ny, K, vx, vy, dx, eps, Y[i], A[i]);
+        fd_collision(nx, ny, K, vx, vy, w, tau, Y[i], C[i]);
+    }
+    for (int64_t m = 0; m < n; ++m)
+        f[m] = f[m] + dt * ((be[0] * A[0][m] + bi[0] * C[0][m]) + (be[1] * A[1][m] + bi[1] * C[1][m]));
+    if (ystages) {
+        memcpy(ystages, Y[0], sizeof(double) * n);
+        memcpy(ystages + n, Y[1], sizeof(double) * n);
+    }
+}
+
+void or_fd_imex_run(int nx, int ny, int K, const double* vx, const double* vy, const double* w,
+                    double dx, double dt, double tau, double eps, int64_t steps, double* f, double* work) {
+    for (int64_t s = 0; s < steps; ++s) or_fd_imex_step(nx, ny, K, vx, vy, w, dx, dt, tau, eps, f, work, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics: global sums and the projected Fourier amplitude used to fit  */
 /* the decay laws of Eq. (shear_sol) and Eq. (taylor).                        */
 /* out = {sum rho, sum rho ux, sum rho uy, A} with                           */

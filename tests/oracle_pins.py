@@ -517,13 +517,13 @@ def check_fd_linear_modes(mutant=0):
         assert rel < 1e-7, (n, rel)
 
 
-def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
-    """Brute-force FD update in mpmath, written out from the definitions:
+def _fd_mp_ops(nodes, weights, nx, ny, dx, tau, eps, mp):
+    """The FD right-hand side in mpmath, written out from the definitions:
     Jiang-Shu WENO-5 interface values upwinded by the sign of each velocity
-    component (v = 0: no advection), conservative flux differences, BGK with
-    the moments of the stage input, SSP-RK3 in Shu-Osher form; periodic."""
+    component (v = 0: no advection) in conservative flux differences (A), and
+    BGK with the moments of the state it acts on (C). Periodic."""
     n = len(nodes)
-    K, ny, nx = n * n, len(f[0]), len(f[0][0])
+    K = n * n
     v = [(nodes[k % n], nodes[k // n]) for k in range(K)]
     w = [weights[k % n] * weights[k // n] for k in range(K)]
 
@@ -545,7 +545,7 @@ def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
                 F.append(face(*[g[(i + 2 - s) % m] for s in range(5)]))
         return [F[(i + 1) % m] - F[i] for i in range(m)]
 
-    def L(g):
+    def A(g):
         out = [[[mp.mpf(0)] * nx for _ in range(ny)] for _ in range(K)]
         for k in range(K):
             if v[k][0] != 0:
@@ -558,6 +558,10 @@ def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
                     d = line_flux_diff([g[k][y][x] for y in range(ny)], v[k][1])
                     for y in range(ny):
                         out[k][y][x] -= v[k][1] * d[y] / dx
+        return out
+
+    def feq(g):
+        out = [[[mp.mpf(0)] * nx for _ in range(ny)] for _ in range(K)]
         for y in range(ny):
             for x in range(nx):
                 rho = sum(g[k][y][x] for k in range(K))
@@ -566,12 +570,26 @@ def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
                 usq = ux * ux + uy * uy
                 for k in range(K):
                     xi = v[k][0] * ux + v[k][1] * uy
-                    feq = w[k] * rho * (1 + xi + xi * xi / 2 - usq / 2)
-                    out[k][y][x] -= (g[k][y][x] - feq) / tau
+                    out[k][y][x] = w[k] * rho * (1 + xi + xi * xi / 2 - usq / 2)
         return out
+
+    def C(g):
+        e = feq(g)
+        return [[[-(g[k][y][x] - e[k][y][x]) / tau for x in range(nx)] for y in range(ny)] for k in range(K)]
 
     def axpy(a, x, b, y):
         return [[[a * x[k][j][i] + b * y[k][j][i] for i in range(nx)] for j in range(ny)] for k in range(K)]
+
+    return A, C, feq, axpy
+
+
+def _fd_mp_run(f, nodes, weights, dx, dt, tau, eps, steps, mp):
+    """Brute-force FD update in mpmath (_fd_mp_ops), SSP-RK3 in Shu-Osher form."""
+    K, ny, nx = len(f), len(f[0]), len(f[0][0])
+    A, C, _, axpy = _fd_mp_ops(nodes, weights, nx, ny, dx, tau, eps, mp)
+
+    def L(g):
+        return axpy(1, A(g), 1, C(g))
 
     for _ in range(steps):
         f1 = axpy(1, f, dt, L(f))
@@ -607,6 +625,181 @@ def check_fd_high_precision(mutant=0):
         fo = oracle.fd_run(f0, dx, dt, tau, steps, eps=eps, mutant=mutant)
         err = np.max(np.abs(fo - exact)) / np.max(np.abs(exact))
         assert err < 1e-13, (n, err)
+
+
+# ---------------------------------------------------------------- FD, IMEX
+# IMEX-SSP2(2,2,2) (Pareschi and Russo 2005): explicit and implicit tableaux.
+IMEX_G = 1.0 - 1.0 / math.sqrt(2.0)
+IMEX_AE = np.array([[0.0, 0.0], [1.0, 0.0]])
+IMEX_AI = np.array([[IMEX_G, 0.0], [1.0 - 2.0 * IMEX_G, IMEX_G]])
+IMEX_BE = np.array([0.5, 0.5])
+IMEX_BI = np.array([0.5, 0.5])
+
+
+def _imex_linear_step_matrix(Ah, Ch, dt):
+    """One IMEX Runge-Kutta step of the linear system y' = Ah y + Ch y (Ah
+    explicit, Ch implicit), built from the tableaux by generic linear solves:
+    (I - dt a_ii Ch) Y_i = y + dt sum_{j<i} (a~_ij Ah + a_ij Ch) Y_j,
+    y' = y + dt sum_i (b~_i Ah + b_i Ch) Y_i. Returns the matrix y -> y'."""
+    K = Ah.shape[0]
+    I = np.eye(K, dtype=complex)
+    Ys = []
+    for i in range(2):
+        rhs = I.copy()
+        for j in range(i):
+            rhs = rhs + dt * (IMEX_AE[i, j] * Ah + IMEX_AI[i, j] * Ch) @ Ys[j]
+        Ys.append(np.linalg.solve(I - dt * IMEX_AI[i, i] * Ch, rhs))
+    G = I.copy()
+    for i in range(2):
+        G = G + dt * (IMEX_BE[i] * Ah + IMEX_BI[i] * Ch) @ Ys[i]
+    return G
+
+
+def check_imex_relaxation(mutant=0):
+    """Spatially uniform state (no advection): f - f^eq is multiplied per step
+    by the implicit tableau's stability function R(z) = 1 + z b^T (I - z A)^-1 1,
+    z = -dt/tau (second order: R = e^z + O(z^3); L-stable: R(-inf) = 0), for
+    non-stiff and stiff dt/tau. The scheme's update f + dt sum b_i C(Y_i)
+    evaluates C(Y) = -(Y - f^eq)/tau by cancellation, so its rounding grows
+    with dt/tau: the tolerance does too."""
+    one = np.ones(2)
+    for n in (4, 5):
+        K = n * n
+        feq = oracle.feq_cell(n, 1.05, 0.02, -0.03, mutant)
+        pert = wl.random_uniform(K, seed=150 + n, lo=-1e-3, hi=1e-3)
+        f0 = np.repeat(np.repeat((feq + pert)[:, None, None], 4, 1), 5, 2).copy()
+        r, ux, uy = oracle.macro(n, f0, mutant)
+        fe = oracle.equilibrium(n, r, ux, uy, mutant)
+        for ratio in (0.5, 5.0, 50.0):
+            tau = 1e-3
+            dt = ratio * tau
+            z = -ratio
+            R = 1 + z * IMEX_BI @ np.linalg.solve(np.eye(2) - z * IMEX_AI, one)
+            f1 = oracle.fd_imex_run(f0, 0.1, dt, tau, 1, 1e-6, mutant)
+            assert np.allclose(f1 - fe, R * (f0 - fe), rtol=0, atol=1e-15 * (1 + ratio)), (n, ratio)
+    # the tableau itself: second order in z, L-stable
+    for z in (-1e-3, -2e-3):
+        R = 1 + z * IMEX_BI @ np.linalg.solve(np.eye(2) - z * IMEX_AI, one)
+        assert abs(R - math.exp(z)) < 0.1 * abs(z) ** 3
+    assert abs(1 - IMEX_BI @ np.linalg.solve(IMEX_AI, one)) < 1e-15
+
+
+def check_imex_stiff_limit(mutant=0):
+    """tau -> 0: the first stage relaxes to the equilibrium of f^n in one
+    stage, every stage keeps the moments of its explicit part (the collision
+    conserves rho and rho u), and the step stays finite."""
+    n = 4
+    rho, ux, uy = wl.random_smooth(8, 6, seed=160, amp_rho=0.1, amp_u=0.1)
+    f0 = oracle.equilibrium(n, rho, ux, uy, mutant)
+    f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=161, lo=-0.05, hi=0.05))
+    r, u, v = oracle.macro(n, f0, mutant)
+    fe = oracle.equilibrium(n, r, u, v, mutant)
+    dt = 1e-2
+    f1, (y1, y2) = oracle.fd_imex_stages(f0, 1 / 8, dt, 1e-14 * dt, 1e-6, mutant)
+    assert np.max(np.abs(y1 - fe)) < 1e-12 * np.max(np.abs(fe))
+    assert np.all(np.isfinite(f1))
+    # moments of Y_1 = moments of f^n (Z_1 = f^n)
+    m0 = oracle.macro(n, f0, mutant)
+    m1 = oracle.macro(n, y1, mutant)
+    for a, b in zip(m0, m1):
+        assert np.max(np.abs(a - b)) < 1e-12
+
+
+def check_imex_linear_modes(mutant=0):
+    """IMEX shear-wave amplitude equals the exact linear prediction: the
+    symbol of the linear-weight WENO-5 (D5) for each upwind direction as the
+    explicit operator, the linearised BGK as the implicit one, and the step
+    matrix built from the two tableaux by generic linear solves
+    (_imex_linear_step_matrix), for the 3-, 4- and 5-node sets, at dt/tau = 0.5
+    and at dt/tau = 5 (stiff for the explicit scheme)."""
+    U = 1e-4
+    for n in (3, 4, 5):
+        K = n * n
+        vx, vy, w = oracle.velocity_set(n)
+        nx, ny = 16, 2
+        dx = 1.0 / nx
+        th = 2 * math.pi / nx
+        m = np.arange(-3, 4)
+        ap = np.array([-2, 15, -60, 20, 30, -3, 0]) / 60.0
+        an = -ap[::-1]
+        sym_p = np.sum(ap * np.exp(1j * th * m)) / dx
+        sym_n = np.sum(an * np.exp(1j * th * m)) / dx
+        adv = np.array([vx[k] * (sym_p if vx[k] > 0 else sym_n) if vx[k] != 0 else 0.0 for k in range(K)])
+        for dt, tau in ((2e-3, 4e-3), (5e-3, 1e-3)):
+            G = _imex_linear_step_matrix(-np.diag(adv), -(np.eye(K) - _linear_E(vx, vy, w)) / tau, dt)
+            steps = 40
+            pred = _shear_amplitude_linear(G, vx, vy, w, U, 0, steps)
+            rho, ux, uy = wl.shear_wave(nx, ny, U)
+            comp, px, py, norm = wl.probe_shear(nx, ny)
+            f = oracle.equilibrium(n, rho, ux, uy, mutant)
+            got = []
+            for _ in range(steps + 1):
+                got.append(oracle.observables(f, comp, px, py, norm, mutant)[3])
+                f = oracle.fd_imex_run(f, dx, dt, tau, 1, 1e30, mutant)
+            rel = np.max(np.abs(np.array(got) - pred)) / U
+            assert rel < 1e-7, (n, dt / tau, rel)
+
+
+def check_imex_conservation(mutant=0):
+    """Mass and momentum are invariant under IMEX steps at dt = 10 tau (to the
+    rounding of the scheme's update, which grows with dt/tau: see
+    check_imex_relaxation)."""
+    n = 4
+    rho, ux, uy = wl.random_smooth(16, 12, seed=170, amp_rho=0.1, amp_u=0.1)
+    f = oracle.equilibrium(n, rho, ux, uy, mutant)
+    f = f + wl.random_uniform(f.shape, seed=171, lo=-1e-4, hi=1e-4)
+    px, py = np.ones(16), np.ones(12)
+    o0 = oracle.observables(f, 0, px, py, 1.0, mutant)
+    g = oracle.fd_imex_run(f, 1 / 16, 5e-3, 5e-4, 30, 1e-6, mutant)
+    o1 = oracle.observables(g, 0, px, py, 1.0, mutant)
+    assert abs(o1[0] - o0[0]) < 1e-12 * abs(o0[0])
+    assert abs(o1[1] - o0[1]) < 1e-13 * abs(o0[0]) and abs(o1[2] - o0[2]) < 1e-13 * abs(o0[0])
+
+
+def check_imex_high_precision(mutant=0):
+    """The oracle's IMEX step against a 30-digit mpmath brute force written
+    from the scheme's definitions (_fd_mp_ops), whose implicit stage equations
+    Y = Z + dt a_ii C(Y) are solved by iterating Y <- (Z + lam f^eq(Y)) / (1 + lam)
+    to convergence (no use of the collision's conservation); 16 velocities,
+    6x6 rough state, two steps at dt = 5 tau."""
+    import mpmath as mp
+    mp.mp.dps = 30
+    s6 = mp.sqrt(6)
+    nodes = [-mp.sqrt(3 + s6), -mp.sqrt(3 - s6), mp.sqrt(3 - s6), mp.sqrt(3 + s6)]
+    weights = [(3 - s6) / 12, (3 + s6) / 12, (3 + s6) / 12, (3 - s6) / 12]
+    n, nx, ny = 4, 6, 6
+    K = n * n
+    rho, ux, uy = wl.random_smooth(nx, ny, seed=181, amp_rho=0.2, amp_u=0.1)
+    f0 = oracle.equilibrium(n, rho, ux, uy, mutant)
+    f0 = f0 * (1 + wl.random_uniform(f0.shape, seed=182, lo=-0.2, hi=0.2))
+    dx, dt, tau, eps = 1.0 / nx, 0.02, 0.004, 1e-6
+    A, C, feq, axpy = _fd_mp_ops(nodes, weights, nx, ny, mp.mpf(dx), mp.mpf(tau), mp.mpf(eps), mp)
+    g = mp.mpf(1) - 1 / mp.sqrt(2)
+    ae = [[0, 0], [1, 0]]
+    ai = [[g, 0], [1 - 2 * g, g]]
+    half = mp.mpf(1) / 2
+    f = [[[mp.mpf(float(f0[k, y, x])) for x in range(nx)] for y in range(ny)] for k in range(K)]
+    mdt = mp.mpf(dt)
+    for _ in range(2):
+        As, Cs = [], []
+        for i in range(2):
+            Z = f
+            for j in range(i):
+                Z = axpy(1, Z, mdt * ae[i][j], As[j])
+                Z = axpy(1, Z, mdt * ai[i][j], Cs[j])
+            lam = mdt * ai[i][i] / mp.mpf(tau)
+            Y = Z
+            for _ in range(200):   # contraction with ratio lam / (1 + lam)
+                Y = axpy(1 / (1 + lam), Z, lam / (1 + lam), feq(Y))
+            As.append(A(Y))
+            Cs.append(C(Y))
+        for i in range(2):
+            f = axpy(1, f, mdt * half, As[i])
+            f = axpy(1, f, mdt * half, Cs[i])
+    exact = np.array([[[float(f[k][y][x]) for x in range(nx)] for y in range(ny)] for k in range(K)])
+    fo = oracle.fd_imex_run(f0, dx, dt, tau, 2, eps=eps, mutant=mutant)
+    err = np.max(np.abs(fo - exact)) / np.max(np.abs(exact))
+    assert err < 1e-13, err
 
 
 def check_fd_decay_closed_form(mutant=0):
@@ -714,6 +907,8 @@ ALL_CHECKS = [
     check_weno_quadratic_exact, check_weno_beta, check_weno_linear_weights, check_weno_eno,
     check_fd_linear_advection, check_fd_rk3_relaxation, check_fd_conservation, check_fd_fixed_point,
     check_fd_linear_modes, check_fd_high_precision, check_fd_decay_closed_form,
+    check_imex_relaxation, check_imex_stiff_limit, check_imex_linear_modes, check_imex_conservation,
+    check_imex_high_precision,
     check_units_tables, check_units_time_steps, check_shock_worked_example, check_shock_jump_conditions,
     check_cs_shock_profile,
 ]

@@ -22,6 +22,10 @@ MUTANTS = {
     8: ("WENO: wrong beta_2 coefficient", [P.check_weno_beta, P.check_fd_high_precision]),
     9: ("FD: BGK moments of every stage taken from f^n", [P.check_fd_high_precision, P.check_fd_linear_modes,
                                                           P.check_fd_decay_closed_form]),
+    10: ("IMEX: implicit stages relax to the equilibrium of f^n", [P.check_imex_linear_modes,
+                                                                   P.check_imex_high_precision]),
+    11: ("IMEX: wrong gamma of the implicit tableau", [P.check_imex_relaxation, P.check_imex_linear_modes,
+                                                       P.check_imex_high_precision]),
 }
 
 
