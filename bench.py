@@ -10,18 +10,24 @@ nothing is flushed between steps.
 
 Metric: MLUPS (million lattice-node updates per second) over the workload,
 whole job (all ranks); per-kernel CUDA-event durations give the roofline
-fractions of the dominant kernel (the FD stage) against the FP32 peak and
-the measured HBM copy bandwidth. The same line carries the end-to-end rate
-through the public API (host fields in, observables out), the batched
-(256 mixed lattices, FP32 vs FP64 one at a time) and served (Poisson stream)
-legs, and the FP64 oracle's rate on every host core (cpu_baseline).
+fractions of the dominant kernel (the FD stage) against the FP32 peak
+measured on the same GPU and the measured HBM copy bandwidth. The same line
+carries the end-to-end rate through the public API (host fields in,
+observables out); the batched leg (256 mixed lattices in FP32 against each
+lattice alone in FP64 for the same steps, with the FP32 velocity and
+decay-rate errors); the served leg (a Poisson stream of CS / FD runs of
+64^2..4096^2 nodes and 1k..20k steps into the continuous-batching server:
+p50/p99 latency and slowdown, aggregate rate, FP32 errors of every run up to
+256^2 against FP64); the IMEX leg (FD 16-velocity 4096^2 with tau below the
+Courant-limited step: RK3 at dt = tau against IMEX at the Courant limit);
+and the FP64 oracle's rate on every host core (cpu_baseline).
 
 --impl reference times the FP64 C oracle on the host cores instead (the
 paper publishes no implementation or timings), on bounded samples, one
-oracle process per core. --served-full N runs only the served stream in its
-full configuration (lattices 64^2..4096^2, 1k..20k steps; several minutes).
-Multi-GPU: replicas only (each rank advances its own copy; no collective on
-the data path).
+oracle process per core. --served-full N runs only the served stream with N
+requests at each --served-load. --profile-case cs|fd runs one small lattice
+for kernel profiling. Multi-GPU: replicas only (each rank advances its own
+copy; no collective on the data path).
 """
 from __future__ import annotations
 
@@ -64,9 +70,9 @@ FD_BYTES_LU = 8 * 16 * 4
 # the equilibrium, BGK and stage combination, 3 for the moments.
 WENO5_FLOPS = 64
 FD_FLOPS_LU = 3 * 16 * (2 * (WENO5_FLOPS + 3) + 13 + 3)
-# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops
-# (an FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Nominal FP32 rate per SM and clock, for context beside the measured peak:
+# 128 FP32 lanes x 2 flops (an FMA) per cycle.
+FP32_FLOPS_PER_SM_CYCLE = 128 * 2
 
 
 def peaks():
@@ -288,6 +294,12 @@ def run_gpu(args, rank, world):
     d2h = 2 * 48 / args.steps
 
     peak, peak_kind = peaks()
+    # FP32 peak of this GPU, measured (packed FP32x2 fused multiply-adds on
+    # every SM; the FD stage kernel's WENO-5 arithmetic is packed the same way)
+    from paper_1904_02471_gb300 import lbm as _lbm
+    fp32_flops, n_sm, _ = _lbm.probe_fp32(True)
+    fp32_scalar, _, _ = _lbm.probe_fp32(False)
+    fp32_peak = fp32_flops / 1e12
     gi = {(g["model"], g["q"]): k for k, g in enumerate(groups)}
     gcs, gfd = gi[(0, 3)], gi[(1, 4)]
     K = args.steps
@@ -335,9 +347,13 @@ def run_gpu(args, rank, world):
             "finalize_ms_per_step": round(fin_ms, 4),
         },
         "roofline": {"kernel": f"fd_stage_kernel<float,4,{fd_ty}> (FD RK stage, Q=16)", "bound": "alu",
-                     "achieved": round(fd_tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                     "frac": round(fd_tflops / FP32_PEAK_TFLOPS, 4),
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                     "achieved": round(fd_tflops, 2), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(fd_tflops / fp32_peak, 4),
+                     "peak_source": f"measured on this GPU: independent packed FP32x2 fused multiply-add chains "
+                                    f"on all {n_sm} SMs, CUDA events (lbm_probe_fp32); one FMA per instruction: "
+                                    f"{fp32_scalar / 1e12:.2f} TFLOP/s; nominal {n_sm} SMs x 256 flops/cycle x "
+                                    f"{(clk.get('sm_mhz') or 2070):.0f} MHz = "
+                                    f"{n_sm * FP32_FLOPS_PER_SM_CYCLE * (clk.get('sm_mhz') or 2070) / 1e6:.1f}",
                      "traffic": traffic.get("fd_stage") if traffic else None,
                      "algorithmic_flops_per_launch": FD_N * FD_N * FD_FLOPS_LU // 3,
                      "algorithmic_bytes_per_launch": FD_N * FD_N * FD_BYTES_LU // 3,
@@ -352,7 +368,9 @@ def run_gpu(args, rank, world):
     }
     if not args.no_extras:
         rec["batched"] = run_batched(torch)
-        rec["served"] = run_served(torch)
+        rec["imex"] = run_imex(torch)
+        rec["served"] = run_served(torch, n_req=args.served_requests, load=args.served_load[0],
+                                   chunk=args.served_chunk)
     if rates is not None:
         rec["cpu_baseline"] = {
             "value": round(sum(cpu_value(r) for r in rates_all), 4), "unit": "MLUPS", "cores": ncores, "kind": "oracle",
@@ -393,114 +411,133 @@ def _fields(d):
     return wl.shear_wave(n, n, U) if d.get("init") == "shear" else wl.taylor_green(n, n, U)
 
 
-def run_batched(torch, steps=192, plain_steps=2):
+def _probe(d, n):
+    """Amplitude probe of an instance's initial mode (shear or Taylor-Green)."""
+    return wl.probe_shear(n, n) if d.get("init") == "shear" else wl.probe_taylor_green(n, n)
+
+
+def _decay_rates(s32, s64, skip_frac=0.25, floor=1e-3):
+    """Decay rates gamma (A ~ exp(-gamma t)) of an FP32 and an FP64 amplitude
+    series of the same run, each by the library's log-linear least squares
+    over the same window: t >= skip_frac * t_end, and only while the FP64
+    amplitude is above `floor` times its start (past that an FP32 amplitude
+    sits at its rounding floor, far below which FP64 keeps decaying).
+    Returns (g32, g64, ln(A0/A_end) of FP64 over the window)."""
+    import paper_1904_02471_gb300 as pkg
+    t = np.array([o["time"] for o in s64])
+    a64 = np.array([o["amp"] for o in s64])
+    a32 = np.array([o["amp"] for o in s32])[:len(t)]
+    keep = np.abs(a64) >= floor * abs(a64[0])
+    last = int(np.argmin(keep)) if not keep.all() else len(t)
+    last = max(last, 4)
+    t, a64, a32 = t[:last], a64[:last], a32[:last]
+    skip = skip_frac * t[-1]
+    g32, _ = pkg.lbm_fit_decay(t, a32, skip)
+    g64, _ = pkg.lbm_fit_decay(t, a64, skip)
+    return g32, g64, float(math.log(abs(a64[0]) / abs(a64[-1])))
+
+
+def _error_summary(vel, rate, lnd, what, resolved=0.05):
+    """max relative velocity error and relative decay-rate error over a set of
+    lattices (FP32 against FP64 of the same lattice and steps); the decay-rate
+    error also over the lattices whose amplitude decayed by at least
+    ln(A0/A) = `resolved` in the fit window (smaller decays are resolved by
+    FP32 only to its rounding of the amplitude)."""
+    rate, lnd = np.array(rate), np.array(lnd)
+    res = rate[lnd >= resolved]
+    return {
+        "max_rel_velocity_error": float(f"{max(vel):.3e}"),
+        "rel_decay_rate_error": {"max": float(f"{rate.max():.3e}"), "median": float(f"{np.median(rate):.3e}"),
+                                 f"max_where_decay_ln_ge_{resolved}": float(f"{res.max():.3e}") if len(res) else None,
+                                 f"lattices_where_decay_ln_ge_{resolved}": int(len(res))},
+        "lattices": len(vel),
+        "amplitude_decay_ln_range": [float(f"{lnd.min():.3e}"), float(f"{lnd.max():.3e}")],
+        "how": what,
+    }
+
+
+def run_batched(torch, steps=192, warm=32, every=16, max_err_side=256):
     """256 independent lattices (sides from {32..512}, tau* in [0.51, 2], half
     CS, half FD 16-velocity): all advanced together in FP32 (one persistent
     launch per group and step, graph replays) against the plain form, each
-    lattice alone in FP64, one at a time."""
+    lattice alone in FP64, one at a time, for the same steps. Accuracy: every
+    lattice of side <= max_err_side, FP32 batched against its FP64 run."""
     import paper_1904_02471_gb300 as pkg
     inst = wl.batched_instances(256, seed=0)
     cells = sum(d["n"] ** 2 for d in inst)
+    cap = (warm + steps) // every + 2
     B = pkg.Batch([_instance_spec(pkg, d, "fp32") for d in inst])
     for i, d in enumerate(inst):
         B.init(i, *_fields(d))
+        B.set_probe(i, *_probe(d, d["n"]))
     tune = B.tune(2)
-    B.step(32)
+    for i in range(len(inst)):
+        B.record(i, every, cap)
+    B.step(warm)
     B.sync()
     t0 = time.perf_counter()
     B.step(steps)
     B.sync()
     t_b = time.perf_counter() - t0
     mlups_b = cells * steps / t_b / 1e6
-    # accuracy of the FP32 batch against FP64 runs of the same lattices
-    probe = [i for i, d in enumerate(inst) if d["n"] <= 64][:4]
-    got = {i: B.moments(i) for i in probe}
-    done = B.steps_done(probe[0]) if probe else 0
+    sample = [i for i, d in enumerate(inst) if d["n"] <= max_err_side]
+    got = {i: (B.moments(i), B.series(i)) for i in sample}
     B.close()
-    err = 0.0
-    for i in probe:
-        d = inst[i]
-        with pkg.Lattice(**_lat_kwargs(pkg, d, "fp64")) as L:
-            L.init(*_fields(d))
-            L.step(done)
-            _, u, v = L.moments()
-        U = U0 * (math.sqrt(3.0) if d["model"] == "cs" else 1.0)
-        err = max(err, float(np.max(np.abs(got[i][1] - u))) / U, float(np.max(np.abs(got[i][2] - v))) / U)
-    # plain: FP64, one lattice at a time
+    # plain: FP64, one lattice at a time, the same warm-up and timed steps
     t_plain, work = 0.0, 0
     per_model = {"cs": [0, 0.0], "fd": [0, 0.0]}
-    for d in inst:
+    vel, rate, lnd = [], [], []
+    for i, d in enumerate(inst):
         with pkg.Lattice(**_lat_kwargs(pkg, d, "fp64")) as L:
             L.init(*_fields(d))
-            L.step(1)
+            L.set_probe(*_probe(d, d["n"]))
+            L.record(every, cap)
+            L.step(warm)
             L.sync()
             t0 = time.perf_counter()
-            L.step(plain_steps)
+            L.step(steps)
             L.sync()
             dt = time.perf_counter() - t0
+            if i in sample:
+                (_, u32, v32), ser32 = got[i]
+                _, u64, v64 = L.moments()
+                U = U0 * (math.sqrt(3.0) if d["model"] == "cs" else 1.0)
+                vel.append(max(float(np.max(np.abs(u32 - u64))), float(np.max(np.abs(v32 - v64)))) / U)
+                g32, g64, ln64 = _decay_rates(ser32, L.series())
+                rate.append(abs(g32 / g64 - 1.0))
+                lnd.append(ln64)
         t_plain += dt
-        work += d["n"] ** 2 * plain_steps
-        per_model[d["model"]][0] += d["n"] ** 2 * plain_steps
+        work += d["n"] ** 2 * steps
+        per_model[d["model"]][0] += d["n"] ** 2 * steps
         per_model[d["model"]][1] += dt
     mlups_p = work / t_plain / 1e6
     return {
         "workload": "256 lattices, sides uniform in {32,64,128,256,512}, tau* U[0.51,2], half CS D2Q9 / half FD "
                     "16-velocity, shear-wave and Taylor-Green initial states (seed 0); FP32 CS in place",
         "cells": cells,
-        "fp32_batched": {"mlups": round(mlups_b, 1), "steps": steps, "s": round(t_b, 4), "tuning": tune.strip()},
+        "fp32_batched": {"mlups": round(mlups_b, 1), "steps": steps, "untimed_steps_before": warm,
+                         "s": round(t_b, 4), "tuning": tune.strip()},
         "fp64_plain_one_at_a_time": {
-            "mlups": round(mlups_p, 2), "steps_each": plain_steps,
+            "mlups": round(mlups_p, 2), "steps_each": steps, "untimed_steps_before": warm,
             "cs_mlups": round(per_model["cs"][0] / max(per_model["cs"][1], 1e-12) / 1e6, 2),
             "fd_mlups": round(per_model["fd"][0] / max(per_model["fd"][1], 1e-12) / 1e6, 2)},
         "speedup": round(mlups_b / mlups_p, 1),
-        "fp32_vs_fp64_max_rel_velocity_error": float(f"{err:.3e}"),
-        "accuracy_sample": f"{len(probe)} lattices (side <= 64) after {done} steps",
+        "fp32_vs_fp64": _error_summary(
+            vel, rate, lnd, f"every lattice of side <= {max_err_side} ({len(sample)} of 256) after {warm + steps} "
+            "steps: max |u32 - u64| / U over nodes and components; decay rate of the projected amplitude "
+            f"(recorded every {every} steps, log-linear fit over the last 75% of the run while the FP64 amplitude "
+            "is above 1e-3 of its start), |g32/g64 - 1|"),
     }
 
 
 def _lat_kwargs(pkg, d, prec):
     s = _instance_spec(pkg, d, prec)
     return dict(model="cs" if s.model == 0 else "fd", q=s.q_per_axis, nx=s.nx, ny=s.ny, tau=s.tau, dt=s.dt,
-                precision=prec)
+                precision=prec, storage="inplace" if (s.model == 0 and prec == "fp32") else "ab")
 
 
-def run_served(torch, n_req=100, seed=0, sides=(64, 128, 256, 512, 1024), steps=(1000, 5000), duration_s=30.0,
-               rate_per_s=None, budget_gb=64):
-    """Served stream: Poisson arrivals of CS / FD Taylor-Green runs (FP32)
-    into the continuous-batching server; latency = completion - arrival.
-    The arrival rate is n_req / duration_s unless rate_per_s is given."""
-    import paper_1904_02471_gb300 as pkg
-    from paper_1904_02471_gb300 import lbm
-    rate = rate_per_s if rate_per_s else n_req / duration_s
-    reqs = wl.served_stream(n_req, seed, rate_per_s=rate, sides=sides, steps=steps)
-    work = sum(r["n"] ** 2 * r["steps"] for r in reqs)
-    S = lbm.Server(budget_gb << 30, 256, 128)
-    t0 = time.perf_counter()
-    tickets = []
-    for r in reqs:
-        delay = r["arrival"] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        spec = _instance_spec(pkg, {"model": r["model"], "n": r["n"], "tau_star": r["tau_star"]}, "fp32")
-        U = U0 * (math.sqrt(3.0) if r["model"] == "cs" else 1.0)
-        tickets.append(S.submit(lbm.make_request(spec, r["steps"], "tg", U, obs_every=0)))
-    S.drain(7200)
-    res = [S.poll(t) for t in tickets]
-    S.close()
-    lat = sorted(x["t_done"] - x["t_submit"] for x in res)
-    makespan = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
-    ok = sum(1 for x in res if x["status"] == 0)
-    span = reqs[-1]["arrival"]
-    return {
-        "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{span:.0f} s, CS or FD 16-velocity "
-                    f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2), steps U[{steps[0]},{steps[1]}], FP32 "
-                    "(CS in place)",
-        "requests": n_req, "completed_ok": ok,
-        "aggregate_mlups": round(work / makespan / 1e6, 1),
-        "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4), "p99": round(float(np.percentile(lat, 99)), 4),
-                      "max": round(lat[-1], 4)},
-        "makespan_s": round(makespan, 3),
-    }
+SERVED_SIDES = (64, 128, 256, 512, 1024, 2048, 4096)
+SERVED_STEPS = (1000, 20000)
 
 
 def lattice_rates(torch, sides, steps=8):
@@ -526,27 +563,150 @@ def lattice_rates(torch, sides, steps=8):
     return rates
 
 
-def run_served_full(torch, n_req, loads, seed=0):
-    """The served-stream configuration in full: sides 64^2..4096^2, 1k..20k
-    steps. The arrival rate is set to `load` times an estimate of the
-    capacity: the mean service time of a request of the stream, each lattice
-    run alone at its measured single-lattice rate (an underestimate of the
-    server's capacity, which batches small lattices)."""
-    sides = (64, 128, 256, 512, 1024, 2048, 4096)
-    steps = (1000, 20000)
-    rates = lattice_rates(torch, sides)
+def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERVED_STEPS, budget_gb=128,
+               chunk=128, max_err_side=256, rates=None):
+    """Served stream: Poisson arrivals of CS / FD 16-velocity Taylor-Green runs
+    (FP32, sides log-uniform over powers of two, steps uniform) into the
+    continuous-batching server; latency = completion - arrival. The arrival
+    rate is `load` times an estimate of the capacity: the mean service time
+    of the stream's requests, each lattice run alone at its measured rate (an
+    underestimate of the server's capacity, which batches small lattices).
+    Accuracy: every run of side <= max_err_side keeps its final fields and
+    records its amplitude, and is compared with the same run in FP64."""
+    import paper_1904_02471_gb300 as pkg
+    from paper_1904_02471_gb300 import lbm
+    if rates is None:
+        rates = lattice_rates(torch, sides)
     probe = wl.served_stream(n_req, seed, rate_per_s=1.0, sides=sides, steps=steps)
     service = sum(r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in probe) / n_req
+    rate = load / service
+    reqs = wl.served_stream(n_req, seed, rate_per_s=rate, sides=sides, steps=steps)
+    work = sum(r["n"] ** 2 * r["steps"] for r in reqs)
+    sample = [i for i, r in enumerate(reqs) if r["n"] <= max_err_side]
+    obs_every = {i: max(1, reqs[i]["steps"] // 32) for i in sample}
+    S = lbm.Server(budget_gb << 30, 256, chunk)
+    t0 = time.perf_counter()
+    tickets = []
+    for i, r in enumerate(reqs):
+        delay = r["arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        spec = _instance_spec(pkg, {"model": r["model"], "n": r["n"], "tau_star": r["tau_star"]}, "fp32")
+        U = U0 * (math.sqrt(3.0) if r["model"] == "cs" else 1.0)
+        tickets.append(S.submit(lbm.make_request(spec, r["steps"], "tg", U, obs_every=obs_every.get(i, 0),
+                                                 keep_moments=i in sample)))
+    S.drain(7200)
+    res = [S.poll(t) for t in tickets]
+    kept = {i: (S.moments(tickets[i], reqs[i]["n"], reqs[i]["n"]), S.series(tickets[i])) for i in sample
+            if res[i]["status"] == 0}
+    for t in tickets:
+        S.release(t)
+    S.close()
+    lat = sorted(x["t_done"] - x["t_submit"] for x in res)
+    makespan = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+    ok = sum(1 for x in res if x["status"] == 0)
+    span = reqs[-1]["arrival"]
+    # the same runs in FP64 (one batch, each with its own step budget)
+    vel, rdec, lnd = [], [], []
+    if kept:
+        idx = sorted(kept)
+        specs = [_instance_spec(pkg, {"model": reqs[i]["model"], "n": reqs[i]["n"],
+                                      "tau_star": reqs[i]["tau_star"]}, "fp64") for i in idx]
+        B = pkg.Batch(specs)
+        for b, i in enumerate(idx):
+            n = reqs[i]["n"]
+            U = U0 * (math.sqrt(3.0) if reqs[i]["model"] == "cs" else 1.0)
+            B.init(b, *wl.taylor_green(n, n, U))
+            B.set_probe(b, *wl.probe_taylor_green(n, n))
+            B.record(b, obs_every[i], reqs[i]["steps"] // obs_every[i] + 1)
+            B.set_budget(b, reqs[i]["steps"])
+        B.step(max(reqs[i]["steps"] for i in idx))
+        B.sync()
+        for b, i in enumerate(idx):
+            (_, u32, v32), ser32 = kept[i]
+            _, u64, v64 = B.moments(b)
+            U = U0 * (math.sqrt(3.0) if reqs[i]["model"] == "cs" else 1.0)
+            vel.append(max(float(np.max(np.abs(u32 - u64))), float(np.max(np.abs(v32 - v64)))) / U)
+            g32, g64, ln64 = _decay_rates(ser32, B.series(b))
+            rdec.append(abs(g32 / g64 - 1.0))
+            lnd.append(ln64)
+        B.close()
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    # slowdown: latency over the run's time alone at its measured single-lattice rate
+    alone = [r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in reqs]
+    late = [x["t_done"] - x["t_submit"] for x in res]
+    slow = sorted(l / a for l, a in zip(late, alone))
+    worst = max(range(n_req), key=lambda i: late[i])
+    out = {
+        "workload": f"{n_req} Poisson arrivals (seed {seed}) over ~{span:.0f} s, CS D2Q9 (in place) or FD 16-velocity "
+                    f"Taylor-Green, sides {sides[0]}..{sides[-1]} (powers of 2, log-uniform), steps "
+                    f"U[{steps[0]},{steps[1]}], tau* U[0.51,2], FP32",
+        "requests": n_req, "completed_ok": ok, "load": load, "rate_per_s": round(rate, 5),
+        "mean_service_s_alone": round(service, 3), "chunk_steps": chunk,
+        "aggregate_mlups": round(work / makespan / 1e6, 1),
+        "latency_s": {"p50": round(p50, 4), "p99": round(p99, 4), "max": round(lat[-1], 4),
+                      "p99_over_p50": round(p99 / p50, 2)},
+        "slowdown": {"p50": round(float(np.percentile(slow, 50)), 2), "p99": round(float(np.percentile(slow, 99)), 2),
+                     "max": round(slow[-1], 2), "how": "latency / the run's time alone at its single-lattice rate"},
+        "longest_latency_run": {"model": reqs[worst]["model"], "side": reqs[worst]["n"],
+                                "steps": reqs[worst]["steps"], "arrival_s": round(reqs[worst]["arrival"], 2),
+                                "alone_s": round(alone[worst], 2), "latency_s": round(late[worst], 2)},
+        "makespan_s": round(makespan, 3),
+        "runs": {"columns": ["model", "side", "steps", "arrival_s", "latency_s"],
+                 "rows": [[r["model"], r["n"], r["steps"], round(r["arrival"], 2), round(x["t_done"] - x["t_submit"], 3)]
+                          for r, x in zip(reqs, res)]},
+    }
+    if vel:
+        out["fp32_vs_fp64"] = _error_summary(
+            vel, rdec, lnd, f"every run of side <= {max_err_side} ({len(vel)} of {n_req}), its kept final fields "
+            "against the same run in FP64: max |u32 - u64| / U; decay rate of the projected amplitude (recorded "
+            "every steps/32 steps, log-linear fit over the last 75% of the run while the FP64 amplitude is above "
+            "1e-3 of its start), |g32/g64 - 1|")
+    return out
+
+
+def run_imex(torch, n=FD_N, tau=1e-5, steps=24, warm=3):
+    """FD 16-velocity FP32 on an n^2 lattice in the stiff regime (tau = 1e-5
+    FD units, below the Courant-limited step 0.4 dx / max|v|): SSP-RK3 at its
+    largest admitted step dt = tau against IMEX-SSP2(2,2,2) at the Courant
+    limit. Per-stage CUDA-event times; physical time advanced per second of
+    device time is the figure that decides between them."""
+    import paper_1904_02471_gb300 as pkg
+    dt_cfl = FD_CFL * pkg.lbm_fd_max_dt(4, 1.0 / n, 1e300)
+    out = {"lattice": [n, n], "velocities": 16, "tau_fd": tau, "precision": "fp32", "steps": steps}
+    for scheme, dt in (("rk3", min(tau, dt_cfl)), ("imex", dt_cfl)):
+        spec = pkg.make_spec("fd", 4, n, n, tau, dt, 0.0, "fp32", scheme=scheme)
+        B = pkg.Batch([spec])
+        B.init(0, *wl.taylor_green(n, n, U0))
+        B.record(0, steps, 4)
+        B.step_profiled(warm)
+        ms, total = B.step_profiled(steps)
+        ser = B.series(0)
+        B.close()
+        nst = 2 if scheme == "imex" else 3
+        stage = [float(ms[0][k]) / steps for k in range(nst)]
+        step_ms = sum(stage)
+        bytes_lu = (6 if scheme == "imex" else 8) * 16 * 4
+        out[scheme] = {"dt": dt, "dt_over_tau": round(dt / tau, 4), "stages": nst,
+                       "stage_ms": [round(x, 4) for x in stage], "ms_per_step": round(step_ms, 4),
+                       "mlups": round(n * n / (step_ms / 1e3) / 1e6, 1),
+                       "gbs": round(n * n * bytes_lu / (step_ms / 1e3) / 1e9, 1), "bytes_per_lu": bytes_lu,
+                       "physical_time_per_s": round(dt / (step_ms / 1e3), 6),
+                       "finite": all(x["nonfinite"] == 0 for x in ser)}
+    out["imex_over_rk3_physical_time_rate"] = round(out["imex"]["physical_time_per_s"] /
+                                                    out["rk3"]["physical_time_per_s"], 3)
+    return out
+
+
+def run_served_full(torch, n_req, loads, seed=0, chunk=128):
+    """The served stream at several loads (one record)."""
+    sides = SERVED_SIDES
+    rates = lattice_rates(torch, sides)
     out = {"metric": "served stream, full configuration", "unit": "MLUPS", "dtype": "f32",
            "data": "synthetic (Taylor-Green initial states, seeded arrivals)",
-           "single_lattice_mlups": {f"{m}{n}": round(v / 1e6, 1) for (m, n), v in rates.items()},
-           "mean_service_s_alone": round(service, 3), "runs": []}
+           "single_lattice_mlups": {f"{m}{n}": round(v / 1e6, 1) for (m, n), v in rates.items()}, "runs": []}
     for load in loads:
-        rec = run_served(torch, n_req=n_req, seed=seed, sides=sides, steps=steps, rate_per_s=load / service,
-                         budget_gb=128)
-        rec["load"] = load
-        rec["rate_per_s"] = round(load / service, 5)
-        out["runs"].append(rec)
+        out["runs"].append(run_served(torch, n_req=n_req, load=load, seed=seed, rates=rates, chunk=chunk))
     return out
 
 
@@ -578,33 +738,77 @@ def committed_traffic():
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The FP64 C oracle on the host cores (the paper publishes no
+    implementation or timings). Each timed step is one bounded sample per
+    process: CS D2Q9 512^2 and FD 16-velocity 128^2 for a share of the CPU
+    budget each, one independent single-thread process per host core, all at
+    once. `value` combines the measured per-node-update rates of the two
+    models in the proportions of the roofline workload (8192^2 CS nodes and
+    4096^2 FD nodes per step); `ms_per_step` is the wall time of one sample
+    step of this run."""
     if rank != 0:
         return None
     import oracle  # noqa: F401
     ncores = host_cores()
-    vals, per_steps = [], []
+    vals, walls = [], []
     rates = None
     with oracle_pool(ncores) as pool:
         for s in range(args.warmup + args.steps):
+            w0 = time.perf_counter()
             rs = oracle_rates_all_cores(pool, ncores, args.cpu_budget / max(1, args.steps))
+            w = time.perf_counter() - w0
             if s >= args.warmup:
-                v = sum(cpu_value(r) for r in rs)
-                vals.append(v)
-                per_steps.append((CS_N * CS_N + FD_N * FD_N) / (v * 1e6))
+                vals.append(sum(cpu_value(r) for r in rs))
+                walls.append(w)
             rates = rs[0]
     val = statistics.median(vals)
-    per_step_s = statistics.median(per_steps)
-    sample = (f"{rates['cs_sample']}; {rates['fd_sample']} per step and process; FP64 C oracle, one independent "
+    sample = (f"per step and process: {rates['cs_sample']}; {rates['fd_sample']}; FP64 C oracle, one independent "
               f"single-thread process per host core ({ncores}) at once, rates summed")
     return {
         "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_s * 1e3, 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.median(walls) * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (Taylor-Green initial state)",
-        "config": {"workload": WORKLOAD, "reference": "plain FP64 C oracle (no published implementation)"},
+        "config": {"workload": WORKLOAD, "reference": "plain FP64 C oracle (no published implementation)",
+                   "ran": sample,
+                   "value_is": "the measured CS and FD per-node-update rates of the samples, combined in the "
+                               "workload's proportions (8192^2 CS + 4096^2 FD nodes per step): extrapolated per "
+                               "node update, not a run of the full lattices",
+                   "ms_per_step_is": "wall time of one timed sample step of this run"},
         "cpu_baseline": {"value": round(val, 4), "unit": "MLUPS", "cores": ncores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(val, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def run_profile_case(a):
+    """One small single lattice for kernel profiling (e.g. under Nsight
+    Compute): a Taylor-Green lattice in FP32 deviation storage whose state is
+    larger than the 129 MB L2 (CS 2048^2: 302 MB; FD 16-velocity 1024^2:
+    201 MB) but small enough that a multi-pass capture ends in seconds. The
+    kernel variant can be pinned with --tile, the grid with --grid (0: one
+    block per tile)."""
+    import torch
+    import paper_1904_02471_gb300 as pkg
+    torch.cuda.init()
+    if a.profile_case == "cs":
+        n = a.n or 2048
+        L = pkg.Lattice("cs", 3, n, n, 0.8 / math.sqrt(3), precision=a.precision, storage=a.storage)
+        if a.tile >= 0:
+            L.config(a.tile, a.grid)
+        L.init(*wl.taylor_green(n, n, 0.01 * math.sqrt(3)))
+        L.step(a.case_steps or 4)
+    else:
+        n = a.n or 1024
+        # IMEX: dt = 5 tau (a step the RK3 scheme refuses)
+        tau = 2e-6 if a.scheme == "imex" else 5e-4
+        L = pkg.Lattice("fd", a.q, n, n, tau, dt=1e-5, precision=a.precision, scheme=a.scheme)
+        if a.tile >= 0:
+            L.config(a.tile, a.grid)
+        L.init(*wl.taylor_green(n, n, 0.01))
+        L.step(a.case_steps or 2)
+    L.sync()
+    print(a.profile_case, n, "mass", L.observables()["mass"])
+    L.close()
 
 
 def main():
@@ -616,15 +820,31 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
+    ap.add_argument("--served-requests", type=int, default=48, help="requests of the served stream")
+    ap.add_argument("--served-load", type=float, nargs="+", default=[1.0],
+                    help="arrival rate as a multiple of the estimated capacity (the line uses the first)")
+    ap.add_argument("--served-chunk", type=int, default=128, help="the server's chunk_steps")
     ap.add_argument("--served-full", type=int, default=0, metavar="N_REQ",
-                    help="only run the served stream in its full configuration (sides up to 4096^2, up to 20k "
-                         "steps) with N_REQ requests, at each --served-load, and print that record")
-    ap.add_argument("--served-load", type=float, nargs="+", default=[1.0, 1.5])
+                    help="only run the served stream with N_REQ requests at each --served-load and print that "
+                         "record")
+    ap.add_argument("--profile-case", choices=["cs", "fd"], default=None,
+                    help="only run one small lattice for kernel profiling (see run_profile_case)")
+    ap.add_argument("--n", type=int, default=0, help="--profile-case: lattice side")
+    ap.add_argument("--case-steps", type=int, default=0, help="--profile-case: steps")
+    ap.add_argument("--tile", type=int, default=-1, help="--profile-case: kernel tile variant")
+    ap.add_argument("--grid", type=int, default=0, help="--profile-case: grid (0: one block per tile)")
+    ap.add_argument("--q", type=int, default=4, help="--profile-case fd: nodes per axis")
+    ap.add_argument("--precision", default="fp32", help="--profile-case: fp32 or fp64")
+    ap.add_argument("--storage", default="ab", choices=["ab", "inplace"], help="--profile-case cs: storage")
+    ap.add_argument("--scheme", default="rk3", choices=["rk3", "imex"], help="--profile-case fd: time scheme")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.served_full:
         import torch
         torch.cuda.init()
-        print(json.dumps(run_served_full(torch, args.served_full, args.served_load)))
+        print(json.dumps(run_served_full(torch, args.served_full, args.served_load, chunk=args.served_chunk)))
         return
     if args.warmup < 3:
         args.warmup = 3

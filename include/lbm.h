@@ -93,6 +93,17 @@ typedef struct {
 #define LBM_STORE_AB 0
 #define LBM_STORE_INPLACE 1
 
+/* Time integration of an FD lattice. LBM_TS_RK3 (0, the default): the
+ * third-order TVD (SSP) Runge-Kutta scheme of Sec. 2, three stages per step;
+ * it needs dt <= tau (Sec. 4.1, LBM_ESTIFF otherwise). LBM_TS_IMEX: the
+ * second-order IMEX-SSP2(2,2,2) Runge-Kutta scheme of Pareschi and Russo
+ * (2005) with explicit WENO-5 advection and implicit BGK collision, two
+ * stages per step, any dt / tau: Sec. 4.1 notes that implicit-explicit
+ * schemes lift dt < tau but prints none. The CFL bound holds for both. A CS
+ * lattice takes LBM_TS_RK3 (the field is ignored there and must be 0). */
+#define LBM_TS_RK3 0
+#define LBM_TS_IMEX 1
+
 /* Parameters of a lattice. See lbm_create for their meaning. */
 typedef struct {
     int model;        /* LBM_CS or LBM_FD */
@@ -104,6 +115,8 @@ typedef struct {
     double dt;        /* time step (CS: 0 selects 1/sqrt(3)) */
     double dx;        /* node spacing (CS: 0 selects 1; FD: 0 selects 1/nx) */
     double rho0;      /* reference density of the FP32 deviation storage (0 selects 1) */
+    int scheme;       /* FD time integration: LBM_TS_RK3 (0, default) or LBM_TS_IMEX */
+    int reserved;     /* 0 */
 } lbm_spec;
 
 /* ---- unit helpers (Sec. 3) ---------------------------------------------- */
@@ -153,8 +166,10 @@ int lbm_fit_decay(const double* t, const double* a, int64_t n, double t_skip, do
  *  cuda_stream: a cudaStream_t to enqueue work on, or NULL for a stream the
  *      library creates (the legacy default stream is never used).
  * Errors: LBM_EINVAL (bad sizes, model/q pair, tau <= dt/2 for CS, dx/dt),
- *  LBM_ECFL (max|v_ka| dt/dx > 1), LBM_ESTIFF (FD dt > tau), LBM_ENOMEM,
- *  LBM_ECUDA. On error *out is NULL. The state is zero until lbm_init. */
+ *  LBM_ECFL (max|v_ka| dt/dx > 1), LBM_ESTIFF (FD dt > tau with the RK3
+ *  scheme), LBM_ENOMEM, LBM_ECUDA. On error *out is NULL. The state is zero
+ *  until lbm_init. lbm_create makes RK3 lattices; lbm_create_spec takes the
+ *  scheme from the spec. */
 int lbm_create(lbm_ctx** out, int model, int q_per_axis, int nx, int ny, double tau, double dt,
                double dx, int precision, double rho0, void* cuda_stream);
 
@@ -206,7 +221,8 @@ int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
 
 /* Enqueue n >= 0 time steps on the context stream and return. One step is
- * one application of Eq. (sc_evolution) (CS) or one three-stage RK step (FD). */
+ * one application of Eq. (sc_evolution) (CS) or one RK step of the lattice's
+ * scheme (FD: three stages, or two with LBM_TS_IMEX). */
 int lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Wait for all enqueued work. Returns LBM_ECUDA if a kernel failed. */
@@ -349,12 +365,16 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, char* report, size_t report_le
  * U is the velocity amplitude in the model's units. obs_every > 0 records the
  * observables every obs_every steps (fused into the step kernels) and fits
  * the apparent viscosity of the decay (init 0 and 1); 0 records only the
- * first and last state. user_tag is returned unchanged. */
+ * first and last state. keep_moments != 0 keeps the final rho, u fields
+ * (host memory, 24 bytes per node) for lbm_result_moments until the ticket
+ * is released. user_tag is returned unchanged. */
 typedef struct {
     lbm_spec spec;
     int64_t steps;
     int init;
     int obs_every;
+    int keep_moments;
+    int reserved;
     double U;
     double rho_l, rho_r;
     uint64_t user_tag;
@@ -379,18 +399,25 @@ typedef struct {
 
 typedef struct lbm_server lbm_server;
 
-/* Start a server with a worker thread. hbm_budget_bytes bounds the summed
- * device footprint of resident runs (admission control); max_slots bounds
- * their number. Resident runs advance together in scheduling rounds that give
- * each run about the same device time: the run with the cheapest step (by an
- * estimate from its lattice size, model, velocity set and precision) advances
- * chunk_steps steps per round, a run whose step costs m times as much
- * advances chunk_steps / m (at least 1), none more than it has left; so a
- * small run is not held to the pace of a large one. Requests admitted while
- * others run join at the next round. cuda_stream as in lbm_create. A server
- * is thread-safe. LBM_EINVAL for a null out, a zero budget, max_slots < 1 or
- * chunk_steps < 1; LBM_ENOMEM or LBM_ECUDA if the engine cannot be set up
- * (*out is then null). */
+/* Start a server. hbm_budget_bytes bounds the summed device footprint of
+ * resident runs (admission control); max_slots bounds their number. Runs go
+ * to one of two lanes by an estimate of their step's device time (from the
+ * lattice size, model, velocity set and precision): large runs (a step of
+ * about 0.5 ms or more, e.g. a 16-velocity FD lattice from 2048^2 nodes) and
+ * small runs. Each lane has a worker thread and its own CUDA stream, the
+ * small runs' at the device's highest priority and the large runs' at the
+ * lowest, so the two lanes' kernels share the GPU at the same time and a
+ * large run is not throttled by the small runs' rounds. Within a lane,
+ * resident runs advance together in scheduling rounds that give each run
+ * about the same device time: the run with the cheapest step advances the
+ * lane's chunk (chunk_steps for small runs, chunk_steps / 8 for large ones)
+ * per round, a run whose step costs m times as much advances chunk / m (at
+ * least 1), none more than it has left. Requests admitted while others run
+ * join their lane's next round. cuda_stream: NULL for the two streams the
+ * server creates, or a cudaStream_t on which the server then runs a single
+ * lane for all runs. A server is thread-safe. LBM_EINVAL for a null out, a
+ * zero budget, max_slots < 1 or chunk_steps < 1; LBM_ENOMEM or LBM_ECUDA if
+ * the engines cannot be set up (*out is then null). */
 int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, int chunk_steps,
                       void* cuda_stream);
 /* Queue a request and return at once with its ticket. LBM_EINVAL / LBM_ECFL /
@@ -403,12 +430,25 @@ int lbm_poll(lbm_server* s, uint64_t ticket, lbm_result* out);
 /* Copy up to cap recorded observables of a finished run; *count receives how
  * many there are. */
 int lbm_result_series(lbm_server* s, uint64_t ticket, lbm_obs* out, int64_t cap, int64_t* count);
+/* Final fields of a finished run submitted with keep_moments: rho, ux, uy
+ * (host [ny][nx] each, caller-owned), Eq. (f_moments_discrete) of its last
+ * state. LBM_ENOTREADY while the run is not finished, LBM_ENOTFOUND for an
+ * unknown or released ticket or a run without kept fields (or one that
+ * failed before its end). */
+int lbm_result_moments(lbm_server* s, uint64_t ticket, double* rho, double* ux, double* uy);
+/* Forget a finished request: its result, series and kept fields are freed
+ * and later calls with its ticket return LBM_ENOTFOUND. A server keeps every
+ * finished result until it is released (or the server is destroyed), so a
+ * long-lived server should release what it has read. LBM_ENOTREADY for a
+ * queued or running request, LBM_ENOTFOUND for an unknown ticket. */
+int lbm_release(lbm_server* s, uint64_t ticket);
 /* Cancel a queued or running request (a running one stops at the end of the
  * current round with status LBM_ECANCELLED). */
 int lbm_cancel(lbm_server* s, uint64_t ticket);
 /* Wait until every submitted request finished, or timeout_s (LBM_ETIMEOUT). */
 int lbm_server_drain(lbm_server* s, double timeout_s);
-/* Queued, running and finished counts and resident device bytes. */
+/* Queued, running and finished (not yet released) counts and resident
+ * device bytes. */
 int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* finished,
                      size_t* resident_bytes);
 /* Cancel what is left, stop the worker and free everything. */
@@ -475,6 +515,16 @@ int lbm_observables_noalloc(int model, int q_per_axis, int precision, int nx, in
                             int64_t plane, int32_t pitch, int32_t cs_phase, double rho0, int comp, const double* px,
                             const double* py, double norm, int64_t step, double dt, lbm_obs* out,
                             void* cuda_stream);
+
+/* ---- measurement support ------------------------------------------------------
+ * Measured FP32 rate of the current device (no counterpart in the paper; the
+ * denominator of the FD stage kernel's arithmetic roofline): independent
+ * chains of fused multiply-adds on every SM, two per instruction (packed
+ * FP32x2, as the FD kernel uses) when packed != 0, else one; timed with CUDA
+ * events over 10 launches after a warm-up. Writes flops per second (two per
+ * multiply-add), the device's SM count (may be NULL) and the mean launch time
+ * (may be NULL). Synchronous; allocates and frees a small output buffer. */
+int lbm_probe_fp32(int packed, double* flops_per_s, int* sm_count, double* ms_per_launch);
 
 /* ---- errors ---------------------------------------------------------------- */
 const char* lbm_strerror(int code);

@@ -13,7 +13,7 @@
 namespace lbm {
 
 namespace {
-using Key = std::tuple<int, int, int, int>;
+using Key = std::tuple<int, int, int, int, int>;
 std::map<Key, std::pair<int, int>>& cache() {
     static std::map<Key, std::pair<int, int>> m;
     return m;
@@ -42,7 +42,7 @@ int Engine::tune(int trial_steps, std::string* report) {
         if (g.members.empty()) continue;
         long long cells = 0;
         for (int li : g.members) cells += (long long)lat[li].spec.nx * lat[li].spec.ny;
-        const Key key{g.model, g.q1, g.precision, size_class(cells)};
+        const Key key{g.model, g.q1, g.precision, g.scheme, size_class(cells)};
         {
             std::lock_guard<std::mutex> lk(cache_mutex());
             auto it = cache().find(key);
@@ -94,8 +94,8 @@ int Engine::tune(int trial_steps, std::string* report) {
                         if (g.model == LBM_CS) e = launch_cs_step(g.precision, g.tile, g.grid, gd, j, stream_);
                         else {
                             e = cudaSuccess;
-                            for (int st = 1; st <= 3 && e == cudaSuccess; ++st)
-                                e = launch_fd_stage(g.precision, g.q1, g.tile, g.grid, gd, j, st, stream_);
+                            for (int st = 1; st <= fd_stages(g.scheme) && e == cudaSuccess; ++st)
+                                e = launch_fd_stage(g.precision, g.q1, g.scheme, g.tile, g.grid, gd, j, st, stream_);
                         }
                         if (e != cudaSuccess) return e;
                     }

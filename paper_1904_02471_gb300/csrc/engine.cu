@@ -101,8 +101,15 @@ int Engine::validate(const lbm_spec* in, lbm_spec* out) {
             set_error(b);
             return LBM_ECFL;
         }
-        if (s.dt > s.tau * (1.0 + 1e-12)) { set_error("FD requires dt <= tau (non-stiff BGK term, Sec. 4.1)"); return LBM_ESTIFF; }
+        if (s.scheme != LBM_TS_RK3 && s.scheme != LBM_TS_IMEX) { set_error("bad FD scheme"); return LBM_EINVAL; }
+        if (s.scheme == LBM_TS_RK3 && s.dt > s.tau * (1.0 + 1e-12)) {
+            set_error("FD requires dt <= tau with the RK3 scheme (non-stiff BGK term, Sec. 4.1); "
+                      "LBM_TS_IMEX lifts it");
+            return LBM_ESTIFF;
+        }
     }
+    if (s.model == LBM_CS && s.scheme != LBM_TS_RK3) { set_error("the scheme field is for FD lattices"); return LBM_EINVAL; }
+    if (s.reserved != 0) { set_error("lbm_spec.reserved must be 0"); return LBM_EINVAL; }
     if (s.storage != LBM_STORE_AB && s.storage != LBM_STORE_INPLACE) { set_error("bad storage"); return LBM_EINVAL; }
     if (s.storage == LBM_STORE_INPLACE && s.model != LBM_CS) {
         set_error("in-place storage is for CS lattices (FD needs its three stage buffers)");
@@ -137,7 +144,8 @@ void Engine::invalidate_graph() {
 // for every workload measured, e.g. CS D2Q9 8192^2 in place 90 GLUPS against
 // 72 with one block set per SM), one block set per SM for a server's engine,
 // whose lattices change under a captured graph (the blocks then loop over
-// the items).
+// the items), or grid_mult_ block sets, so that each block covers fewer items
+// and retires sooner (SMs then free up for another stream's kernels).
 int Engine::persistent_grid(const Group& g, int tile) const {
     int bps = g.model == LBM_CS ? cs_blocks_per_sm(g.precision, tile) : fd_blocks_per_sm(g.precision, g.q1, tile);
     return (int)std::max<long long>(1, (long long)sm_count_ * bps);
@@ -145,7 +153,7 @@ int Engine::persistent_grid(const Group& g, int tile) const {
 
 int Engine::default_grid(const Group& g, int tile) const {
     if (!dynamic_ && g.total_items > 0) return g.total_items;
-    return persistent_grid(g, tile);
+    return persistent_grid(g, tile) * std::max(1, grid_mult_);
 }
 
 int Engine::open(void* stream) {
@@ -226,12 +234,15 @@ int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
     // group membership: one group per (model, velocity set, storage)
     int gi = -1;
     for (size_t g = 0; g < groups.size(); ++g)
-        if (groups[g].model == s.model && groups[g].q1 == s.q_per_axis && groups[g].precision == s.precision) gi = (int)g;
+        if (groups[g].model == s.model && groups[g].q1 == s.q_per_axis && groups[g].precision == s.precision &&
+            groups[g].scheme == s.scheme)
+            gi = (int)g;
     if (gi < 0) {
         Group g;
         g.model = s.model;
         g.q1 = s.q_per_axis;
         g.precision = s.precision;
+        g.scheme = s.scheme;
         g.tile = s.model == LBM_CS ? (int)CS_B256x32 : (int)FD_T32x8;
         groups.push_back(g);
         gi = (int)groups.size() - 1;
@@ -443,8 +454,8 @@ int Engine::enqueue_chunk(int c) {
                     n += 2;
                 }
             } else {
-                for (int st = 1; st <= 3; ++st) {
-                    e = launch_fd_stage(g.precision, g.q1, g.tile, g.grid, gd, j, st, stream_);
+                for (int st = 1; st <= fd_stages(g.scheme); ++st) {
+                    e = launch_fd_stage(g.precision, g.q1, g.scheme, g.tile, g.grid, gd, j, st, stream_);
                     if (e != cudaSuccess) return cuda_fail(e, "launch_fd_stage");
                     ++n;
                     if (st == 1 && g.any_obs) {
@@ -542,7 +553,7 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
             Group& g = groups[gi];
             if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
             const GroupDev gd = g.dev();
-            const int nk = g.model == LBM_CS ? 1 : 3;
+            const int nk = g.model == LBM_CS ? 1 : fd_stages(g.scheme);
             for (int st = 1; st <= nk; ++st) {
                 static const char* const kNames[4] = {"lbm.cs_step", "lbm.fd_stage1", "lbm.fd_stage2", "lbm.fd_stage3"};
                 NvtxRange kernel_range(kNames[g.model == LBM_CS ? 0 : st]);
@@ -550,7 +561,8 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
                 if (!a || !b) { cleanup(); return cuda_fail(cudaGetLastError(), "cudaEventCreate"); }
                 cudaEventRecord(a, stream_);
                 cudaError_t e = g.model == LBM_CS ? launch_cs_step(g.precision, g.tile, g.grid, gd, 0, stream_)
-                                                  : launch_fd_stage(g.precision, g.q1, g.tile, g.grid, gd, 0, st, stream_);
+                                                  : launch_fd_stage(g.precision, g.q1, g.scheme, g.tile, g.grid, gd, 0, st,
+                                                                    stream_);
                 cudaEventRecord(b, stream_);
                 if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "profiled launch"); }
                 ++launches_;

@@ -69,6 +69,7 @@ struct Lattice {
 
 struct Group {
     int model = 0, q1 = 0, precision = 0;
+    int scheme = LBM_TS_RK3;   // FD time integration
     int tile = 0;
     int grid = 0;
     std::vector<int> members;
@@ -101,6 +102,7 @@ class Engine {
     int remove_lattice(int i);
     static size_t footprint(const lbm_spec& s);  // device bytes of one lattice
     bool dynamic_ = false;   // persistent grids sized for the machine, not the current work
+    int grid_mult_ = 1;      // dynamic engines: blocks per resident block slot (1: one block set per SM)
     int inject_us_ = 0;      // group header word 3 (wait-timeout injection)
     static int validate(const lbm_spec* in, lbm_spec* out);
 

@@ -29,9 +29,12 @@ int fd_tile_ty(int v);
 
 // One CS step (Eq. sc_evolution) for every lattice of the group at sub-step j.
 cudaError_t launch_cs_step(int precision, int tile, int grid, const GroupDev& g, int j, cudaStream_t s);
-// One SSP-RK3 stage (1..3) of the FD update for every lattice of the group.
-cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const GroupDev& g, int j, int stage,
-                            cudaStream_t s);
+// One stage of the FD update for every lattice of the group: scheme
+// LBM_TS_RK3, SSP-RK3 stages 1..3; LBM_TS_IMEX, IMEX-SSP2(2,2,2) stages 1..2.
+cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int grid, const GroupDev& g, int j,
+                            int stage, cudaStream_t s);
+// Stage launches per FD step of a scheme.
+inline int fd_stages(int scheme) { return scheme == LBM_TS_IMEX ? 2 : 3; }
 // Occupancy-based resident CTAs per SM of a variant (for persistent grids).
 int cs_blocks_per_sm(int precision, int tile);
 int fd_blocks_per_sm(int precision, int q1, int tile);

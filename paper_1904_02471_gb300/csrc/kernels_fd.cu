@@ -115,6 +115,64 @@ __device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typ
     return P::div(num, den);
 }
 
+// Column sums cs[ix] = sum_iy g(ix + Q1 iy) and row sums rs[iy] =
+// sum_ix g(ix + Q1 iy) of a quantity over the product set.
+template <typename T, int Q1, typename Fn>
+__device__ __forceinline__ void sum_cols_rows(Fn g, T (&cs)[Q1], T (&rs)[Q1]) {
+#pragma unroll
+    for (int iy = 0; iy < Q1; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) {
+            const T v = g(ix + Q1 * iy);
+            cs[ix] = iy == 0 ? v : cs[ix] + v;
+            rs[iy] = ix == 0 ? v : rs[iy] + v;
+        }
+}
+// Zeroth and first moments from column and row sums: sum g, sum g v_x,
+// sum g v_y (v_x depends on ix only, v_y on iy only).
+template <typename T, int Q1>
+__device__ __forceinline__ void moments_of_sums(const T (&cs)[Q1], const T (&rs)[Q1], T& m0, T& mx, T& my) {
+    m0 = cs[0];
+#pragma unroll
+    for (int i = 1; i < Q1; ++i) m0 += cs[i];
+    mx = T(0);
+    my = T(0);
+#pragma unroll
+    for (int i = 0; i < Q1; ++i) {
+        if (GH<Q1>::v(i) != 0.0) {
+            mx += (T)GH<Q1>::v(i) * cs[i];
+            my += (T)GH<Q1>::v(i) * rs[i];
+        }
+    }
+}
+// v_k . u and v_k . j + d of population k from per-axis products: the 1D set
+// is symmetric (v_{Q1-1-i} = -v_i), so v_i u_x and v_i j_x are formed for
+// the upper half of the nodes and negated for the lower half; v_iy u_y and
+// v_iy j_y + d once per row (shared by the Q1 populations of the row).
+template <typename T, int Q1>
+struct EqTerms {
+    T ux, uy, jx, jy, d;
+    __device__ __forceinline__ T xu(int ix) const {
+        return GH<Q1>::v(ix) == 0.0 ? T(0)
+               : (2 * ix >= Q1 ? (T)GH<Q1>::v(ix) * ux : -((T)GH<Q1>::v(Q1 - 1 - ix) * ux));
+    }
+    __device__ __forceinline__ T xj(int ix) const {
+        return GH<Q1>::v(ix) == 0.0 ? T(0)
+               : (2 * ix >= Q1 ? (T)GH<Q1>::v(ix) * jx : -((T)GH<Q1>::v(Q1 - 1 - ix) * jx));
+    }
+    __device__ __forceinline__ T xi(int k) const {
+        const int ix = k % Q1, iy = k / Q1;
+        if (GH<Q1>::v(iy) == 0.0) return xu(ix);
+        const T yv = (T)GH<Q1>::v(iy) * uy;
+        return GH<Q1>::v(ix) == 0.0 ? yv : xu(ix) + yv;
+    }
+    __device__ __forceinline__ T lin(int k) const {
+        const int ix = k % Q1, iy = k / Q1;
+        const T yl = GH<Q1>::v(iy) == 0.0 ? d : (T)GH<Q1>::v(iy) * jy + d;
+        return GH<Q1>::v(ix) == 0.0 ? yl : xj(ix) + yl;
+    }
+};
+
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -152,11 +210,68 @@ __host__ __device__ constexpr size_t fd_smem_bytes() {
 // threads per SM for FP32, i.e. at most 64 registers per thread (shared
 // memory, 53.5 KiB per 256-thread block for 16 populations, allows as many:
 // four blocks in 228 KiB); 512 threads (128 registers) for FP64.
-template <typename T, int TY>
-constexpr int fd_min_blocks() { return (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) > 0 ? (sizeof(T) == 4 ? 1024 : 512) / (FD_TX * TY) : 1; }
+// The IMEX stage kernels hold more values per thread (the stage input and P
+// at the node): their FP32 variants are bounded for 512 threads per SM (128
+// registers) instead.
+template <typename T, int TY, bool IMEX = false>
+constexpr int fd_min_blocks() {
+    return ((sizeof(T) == 4 ? (IMEX ? 512 : 1024) : 512) / (FD_TX * TY)) > 0
+               ? (sizeof(T) == 4 ? (IMEX ? 512 : 1024) : 512) / (FD_TX * TY)
+               : 1;
+}
 
-template <typename T, int Q1, int TY>
-__global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_kernel(GroupDev g, int j, int stage) {
+// IMEX-SSP2(2,2,2) (LBM_TS_IMEX): gamma of the implicit tableau, 1 - 1/sqrt 2.
+constexpr double IMEX_GAMMA = 0.29289321881345247560;
+
+// IMEX: the implicit BGK part of a stage in closed form, at every staged node
+// of the tile. The stage value Y solves Y = u + dt g C(Y), C(Y) = -(Y -
+// f^eq(Y)) / tau; the collision conserves rho and rho u (Eq. herfeq has the
+// moments of Eq. f_moments_discrete), so Y has the moments of u, f^eq(Y) =
+// f^eq(u), and Y = (u + lam f^eq(u)) / (1 + lam), lam = g dt / tau. Values
+// in the storage form (deviations from w_k rho0 for FP32, r0 = rho0; full f
+// for FP64, r0 = 0): the map is linear, the offsets carry over.
+template <typename T, int Q1>
+__device__ __forceinline__ void imex_stage_values(T* tiles, int hxy, T r0, T lam, T il, int tid, int nt) {
+    constexpr int K = Q1 * Q1;
+    for (int pos = tid; pos < hxy; pos += nt) {
+        T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T u = tiles[k * hxy + pos];
+            dr += u;
+            if (vx_of<Q1>(k) != 0.0) jx += u * (T)vx_of<Q1>(k);
+            if (vy_of<Q1>(k) != 0.0) jy += u * (T)vy_of<Q1>(k);
+        }
+        const T rho = r0 + dr;
+        const T inv = T(1) / rho;
+        const T ux = jx * inv, uy = jy * inv;
+        const T usq = ux * ux + uy * uy, hr = T(0.5) * rho;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T vx = (T)vx_of<Q1>(k), vy = (T)vy_of<Q1>(k);
+            const T xi = vx * ux + vy * uy;
+            const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jx + (vy * jy + dr)));
+            tiles[k * hxy + pos] = (tiles[k * hxy + pos] + lam * geq) * il;
+        }
+    }
+}
+
+// One stage of the FD update. IMEX = false: SSP-RK3 stage `stage` (1..3).
+// IMEX = true: stage 1 or 2 of IMEX-SSP2(2,2,2) with explicit WENO-5
+// advection A and implicit BGK C. With Y_i the stage values (above), the
+// scheme's
+//   Y_2 = f^n + dt A(Y_1) + (1 - 2g) dt C(Y_1) + g dt C(Y_2),
+//   f^{n+1} = f^n + dt/2 (A(Y_1) + A(Y_2) + C(Y_1) + C(Y_2))
+// are evaluated as: stage 1 stages f^n, maps it to Y_1, and writes
+//   Z = f^n + dt A(Y_1) + (1 - 2g) dt C(Y_1)      (buffer 1)
+//   P = f^n + 2g dt C(Y_1)                          (buffer 2);
+// stage 2 stages Z, maps it to Y_2, and writes
+//   f^{n+1} = P + ((Z - P) + dt A(Y_2) + dt C(Y_2)) / 2   (buffer 0),
+// with dt C(Y_i) = -(dt/tau) (u_i - f^eq(u_i)) / (1 + lam), u_i the stage's
+// input (f^n or Z): no difference of nearly equal values is multiplied by
+// dt/tau, so the rounding stays small however stiff the collision is.
+template <typename T, int Q1, int TY, bool IMEX>
+__global__ void __launch_bounds__(FD_TX* TY, (fd_min_blocks<T, TY, IMEX>())) fd_stage_kernel(GroupDev g, int j, int stage) {
     using P = Pr<T>;
     using V = typename P::V;
     constexpr int K = Q1 * Q1;
@@ -189,8 +304,11 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
     const int total = g.hdr[1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    const int in_idx = stage == 1 ? 0 : (stage == 2 ? 1 : 2);
-    const int out_idx = stage == 1 ? 1 : (stage == 2 ? 2 : 0);
+    const int in_idx = IMEX ? (stage == 1 ? 0 : 1) : (stage == 1 ? 0 : (stage == 2 ? 1 : 2));
+    const int out_idx = IMEX ? (stage == 1 ? 1 : 0) : (stage == 1 ? 1 : (stage == 2 ? 2 : 0));
+    // the stage reads its input at its own node from global memory too (IMEX:
+    // the staged tile holds the stage values Y instead), and f^n (RK3 stages 2, 3)
+    const bool node_in = IMEX || stage != 1;
     // stage weights: f^(s) = f^n + cb ((u - f^n) + dt L(u)), i.e. the Shu-Osher
     // combinations 3/4 f^n + 1/4 (u + dt L(u)) and 1/3 f^n + 2/3 (u + dt L(u))
     const T cb = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : T(2.0 / 3.0));
@@ -290,18 +408,35 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
             }
             cp_async_wait_all();
         }
-        const T* __restrict__ fnp = Fn + cell;
+        const T* __restrict__ fnp = (IMEX ? U : Fn) + cell;   // node values of f^n (RK3) / of the input (IMEX)
+        const T* __restrict__ ppn = static_cast<const T*>(dp->buf[2]) + cell;   // IMEX stage 2: P
+        T* __restrict__ pout = static_cast<T*>(dp->buf[2]) + cell;              // IMEX stage 1: P
+        // IMEX constants: lam = g dt/tau, il = 1/(1 + lam), c1 = (dt/tau) il
+        const T lam = T(IMEX_GAMMA) * dtt, il = T(1) / (T(1) + lam), c1 = dtt * il;
         T* __restrict__ op = out + cell;
         __syncthreads();
+        if constexpr (IMEX) {
+            imex_stage_values<T, Q1>(tiles, HXY, r0, lam, il, tid, NT);
+            __syncthreads();
+        }
 
         // 2. moments of the stage input at this node, Eq. (f_moments_discrete)
+        //    (ascending k; FP32 with 16 velocities: through the column sums
+        //    over iy and the row sums over ix of the product set, fewer
+        //    operations)
         T dr = T(0), jx = T(0), jy = T(0);
+        if constexpr (sizeof(T) == 4 && Q1 == 4) {
+            T cs[Q1], rs[Q1];
+            sum_cols_rows<T, Q1>([&](int k) { return tiles[k * HXY + cidx]; }, cs, rs);
+            moments_of_sums<T, Q1>(cs, rs, dr, jx, jy);
+        } else {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const T u = tiles[k * HXY + cidx];
-            dr += u;
-            if (vx_of<Q1>(k) != 0.0) jx += u * (T)vx_of<Q1>(k);
-            if (vy_of<Q1>(k) != 0.0) jy += u * (T)vy_of<Q1>(k);
+            for (int k = 0; k < K; ++k) {
+                const T u = tiles[k * HXY + cidx];
+                dr += u;
+                if (vx_of<Q1>(k) != 0.0) jx += u * (T)vx_of<Q1>(k);
+                if (vy_of<Q1>(k) != 0.0) jy += u * (T)vy_of<Q1>(k);
+            }
         }
         const T rho = r0 + dr;
         const T inv = active ? T(1) / rho : T(0);
@@ -344,36 +479,66 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
         const T hr = T(0.5) * rho;
         T R0 = T(0), R1x = T(0), R1y = T(0);
         if constexpr (sizeof(T) == 4) {
+            // v_k . u and v_k . j + dr from per-axis terms (v_x u_x for each
+            // node of the 1D set, v_y u_y + ... for each row of the product set)
+            const EqTerms<T, Q1> e{ux, uy, jx, jy, dr};
+            auto dk = [&](int k) {
+                T geq;
+                if constexpr (Q1 == 4) {
+                    const T xi = e.xi(k);
+                    geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + e.lin(k));
+                } else {
+                    const T vx = (T)vx_of<Q1>(k), vy = (T)vy_of<Q1>(k);
+                    const T xi = vx * ux + vy * uy;
+                    geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jx + (vy * jy + dr)));
+                }
+                // the stage input at the node (IMEX: from global memory, the
+                // tile holds the stage values)
+                const T uin = IMEX ? ((active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0))
+                                   : tiles[k * HXY + cidx];
+                return uin - geq;
+            };
+            if constexpr (Q1 == 4) {
+                // sums through the columns and rows of the product set
+                T cs[Q1], rs[Q1];
+                sum_cols_rows<T, Q1>(dk, cs, rs);
+                moments_of_sums<T, Q1>(cs, rs, R0, R1x, R1y);
+            } else {
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const T vx = (T)vx_of<Q1>(k), vy = (T)vy_of<Q1>(k);
-                const T xi = vx * ux + vy * uy;
-                const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jx + (vy * jy + dr)));
-                const T d = tiles[k * HXY + cidx] - geq;
-                R0 += d;
-                if (vx_of<Q1>(k) != 0.0) R1x += d * vx;
-                if (vy_of<Q1>(k) != 0.0) R1y += d * vy;
+                for (int k = 0; k < K; ++k) {
+                    const T d = dk(k);
+                    R0 += d;
+                    if (vx_of<Q1>(k) != 0.0) R1x += d * (T)vx_of<Q1>(k);
+                    if (vy_of<Q1>(k) != 0.0) R1y += d * (T)vy_of<Q1>(k);
+                }
             }
         }
         // the correction w_k (R0 + v_k . R1) enters the equilibrium as
         // shifted moments: dr + R0, j + R1
         const T drc = dr + R0, jxc = jx + R1x, jyc = jy + R1y;
+        const EqTerms<T, Q1> ec{ux, uy, jxc, jyc, drc};
 
         // 3. per group of G populations: every thread evaluates the x- and
         //    y-face on the low side of its node for each population of the
-        //    group (one packed pair each), warp p mod TY adds the edge faces
-        //    of the group's p-th population, one barrier, then every node
-        //    updates those G populations from the four faces around it. Two
-        //    face buffers alternate between groups; with one, a barrier also
+        //    group (one packed pair each), the tile's right- and top-edge
+        //    faces are added (below), one barrier, then every node updates
+        //    those G populations from the four faces around it. Two face
+        //    buffers alternate between groups; with one, a barrier also
         //    precedes each group's faces. With the 16-velocity set the packed
         //    pairs are two populations' x-faces and then their y-faces instead
         //    of one population's x- and y-face, and faces are stored and read
-        //    back as pairs (half the shared-memory instructions for them).
+        //    back as pairs (half the shared-memory instructions for them); its
+        //    edge faces are evaluated through one copy of the code for all the
+        //    group's pairs (an unrolled copy per pair and axis had made the
+        //    kernel's instructions outgrow the instruction cache: the warps
+        //    stalled on instruction fetch), the x-edges of all pairs packed one
+        //    (pair, row) per lane.
 #pragma unroll
         for (int k0 = 0; k0 < K; k0 += G) {
             T* fg = faces + (FB == 2 ? ((k0 / G) & 1) * G * NF : 0);
             if (FB == 1 && k0 > 0) __syncthreads();  // the previous group's update is done with the faces
             T fnv[G];
+            T pv[IMEX ? G : 1];   // IMEX stage 2: P at the node
             if constexpr (PAIRS) {
                 // populations 2q and 2q+1 of the group side by side: the x-faces
                 // of both as one packed pair, then the y-faces of both; faces
@@ -396,15 +561,46 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                     };
                     fx2[ty * (TX + 1) + tx] = face(xrow, xo, xs);
                     fy2[ty * TX + tx] = face(ycol, yo, ys);
-                    if (ty == (2 * q) % TY) {
-                        const V f = face(exrow, xo, xs);
-                        if (tx < TY) fx2[tx * (TX + 1) + TX] = f;
-                    }
-                    if (ty == (2 * q + 1) % TY) fy2[TY * TX + tx] = face(eycol, yo, ys);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int k = ka + h;
-                        fnv[2 * q + h] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
+                        fnv[2 * q + h] = (node_in && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
+                        if constexpr (IMEX)
+                            pv[2 * q + h] = (stage == 2 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? ppn[k * plane] : T(0);
+                    }
+                }
+                // the tile's right-edge x-faces and top-edge y-faces of the
+                // group's pairs, through one copy of the code (pair and stencil
+                // direction selected at run time): edge tasks e < NXE are the
+                // right-edge x-faces of all pairs and rows, one (pair, row) per
+                // lane; task NXE + q is pair q's top-edge y-faces, one column
+                // per lane; task e is evaluated by warp e mod TY
+                constexpr int NPR = G / 2;
+                constexpr int NXE = (NPR * TY + 31) / 32;
+                for (int e = ty; e < NXE + NPR; e += TY) {
+                    const bool xax = e < NXE;
+                    const int lx = e * 32 + tx;                    // x task: (pair, row) of this lane
+                    const bool xok = lx < NPR * TY;
+                    const int q = xax ? (xok ? lx / TY : 0) : e - NXE;
+                    const int row = xax ? (xok ? lx % TY : 0) : 0;
+                    const T* ta = tiles + (k0 + 2 * q) * HXY;
+                    const T* tb = ta + HXY;
+                    V* fx2 = reinterpret_cast<V*>(fg) + q * NF;
+                    // pair q's nodes along x are (2q mod Q1, +1): both below the
+                    // middle of the 1D set (v_x < 0) or both above (v_x > 0);
+                    // v_y has one sign in the whole group (whole rows)
+                    const bool xpos = 2 * ((2 * q) % Q1) >= Q1;
+                    const bool ypos = vy_of<Q1>(k0) > 0;
+                    const int st = xax ? (xpos ? 1 : -1) : (ypos ? HXP : -HXP);
+                    const int base = xax ? (row + 3) * HXP + TX + (xpos ? 1 : 6) : eycol + (ypos ? 0 : 5 * HXP);
+                    const T* a = ta + base;
+                    const T* b = tb + base;
+                    const V f = weno5_pair<T>(P::mk(a[0], b[0]), P::mk(a[st], b[st]), P::mk(a[2 * st], b[2 * st]),
+                                              P::mk(a[3 * st], b[3 * st]), P::mk(a[4 * st], b[4 * st]), eps);
+                    if (xax) {
+                        if (xok) fx2[row * (TX + 1) + TX] = f;
+                    } else {
+                        fx2[NFX + TY * TX + tx] = f;
                     }
                 }
             } else {
@@ -437,7 +633,9 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                         if (tx < TY) fx[tx * (TX + 1) + TX] = f.x;
                         fy[TY * TX + tx] = f.y;
                     }
-                    fnv[p] = (stage != 1 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
+                    fnv[p] = (node_in && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? fnp[k * plane] : T(0);
+                    if constexpr (IMEX)
+                        pv[p] = (stage == 2 && active && LBM_BC_NODE(dp, K, cell + k * plane)) ? ppn[k * plane] : T(0);
                 }
             }
             __syncthreads();
@@ -487,14 +685,34 @@ __global__ void __launch_bounds__(FD_TX* TY, fd_min_blocks<T, TY>()) fd_stage_ke
                         const T dc = vyd > 0 ? uk - tk[cidx - HXP] : tk[cidx + HXP] - uk;
                         a += vy * ((fyh - fyl) * T(1.0 / 12.0) + dc);
                     }
-                    const T xi = vx * ux + vy * uy;
-                    const T geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jxc + (vy * jyc + drc)));
-                    // dt L(u)_k = -(dt/dx) a - (u - geq) dt/tau
-                    const T inc = (geq - uk) * dtt - a * cdx;
-                    // stage combination in increment form: one rounding of the
-                    // stored value per stage (u - f^n is exact for close values)
-                    if (LBM_BC_NODE(dp, K, cell + k * plane))
-                        op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
+                    T xi, geq;
+                    if constexpr (sizeof(T) == 4 && Q1 == 4) {
+                        xi = ec.xi(k);
+                        geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + ec.lin(k));
+                    } else {
+                        xi = vx * ux + vy * uy;
+                        geq = (T)w_of<Q1>(k) * (hr * (xi * xi - usq) + (vx * jxc + (vy * jyc + drc)));
+                    }
+                    if constexpr (IMEX) {
+                        // dt A(Y)_k and dt C(Y)_k (from the stage input at the node)
+                        const T dta = -(a * cdx);
+                        const T dtc = -(c1 * (fnv[p] - geq));
+                        if (LBM_BC_NODE(dp, K, cell + k * plane)) {
+                            if (stage == 1) {
+                                op[k * plane] = fnv[p] + (dta + T(1.0 - 2.0 * IMEX_GAMMA) * dtc);   // Z
+                                pout[k * plane] = fnv[p] + T(2.0 * IMEX_GAMMA) * dtc;             // P
+                            } else {
+                                op[k * plane] = pv[p] + T(0.5) * ((fnv[p] - pv[p]) + (dta + dtc));
+                            }
+                        }
+                    } else {
+                        // dt L(u)_k = -(dt/dx) a - (u - geq) dt/tau
+                        const T inc = (geq - uk) * dtt - a * cdx;
+                        // stage combination in increment form: one rounding of the
+                        // stored value per stage (u - f^n is exact for close values)
+                        if (LBM_BC_NODE(dp, K, cell + k * plane))
+                            op[k * plane] = stage == 1 ? uk + inc : fnv[p] + cb * ((uk - fnv[p]) + inc);
+                    }
                 }
             }
         }
@@ -512,23 +730,23 @@ int fd_tile_ty(int v) {
     return 0;
 }
 
-template <typename T, int Q1>
+template <typename T, int Q1, bool IMEX>
 static const void* fd_kernel_ptr_q(int tile) {
     switch (tile) {
-        case FD_T32x8: return (const void*)fd_stage_kernel<T, Q1, 8>;
-        case FD_T32x4: return (const void*)fd_stage_kernel<T, Q1, 4>;
-        case FD_T32x16: return (const void*)fd_stage_kernel<T, Q1, 16>;
-        case FD_T32x2: return (const void*)fd_stage_kernel<T, Q1, 2>;
+        case FD_T32x8: return (const void*)fd_stage_kernel<T, Q1, 8, IMEX>;
+        case FD_T32x4: return (const void*)fd_stage_kernel<T, Q1, 4, IMEX>;
+        case FD_T32x16: return (const void*)fd_stage_kernel<T, Q1, 16, IMEX>;
+        case FD_T32x2: return (const void*)fd_stage_kernel<T, Q1, 2, IMEX>;
     }
     return nullptr;
 }
 
-template <typename T>
+template <typename T, bool IMEX>
 static const void* fd_kernel_ptr(int tile, int q1) {
     switch (q1) {
-        case 3: return fd_kernel_ptr_q<T, 3>(tile);
-        case 4: return fd_kernel_ptr_q<T, 4>(tile);
-        case 5: return fd_kernel_ptr_q<T, 5>(tile);
+        case 3: return fd_kernel_ptr_q<T, 3, IMEX>(tile);
+        case 4: return fd_kernel_ptr_q<T, 4, IMEX>(tile);
+        case 5: return fd_kernel_ptr_q<T, 5, IMEX>(tile);
     }
     return nullptr;
 }
@@ -554,16 +772,18 @@ static size_t fd_smem(int tile, int q1) {
     return 0;
 }
 
-static const void* fd_fn(int precision, int tile, int q1) {
-    return precision == LBM_FP64 ? fd_kernel_ptr<double>(tile, q1) : fd_kernel_ptr<float>(tile, q1);
+static const void* fd_fn(int precision, int tile, int q1, int scheme) {
+    if (scheme == LBM_TS_IMEX)
+        return precision == LBM_FP64 ? fd_kernel_ptr<double, true>(tile, q1) : fd_kernel_ptr<float, true>(tile, q1);
+    return precision == LBM_FP64 ? fd_kernel_ptr<double, false>(tile, q1) : fd_kernel_ptr<float, false>(tile, q1);
 }
 static size_t fd_bytes(int precision, int tile, int q1) {
     return precision == LBM_FP64 ? fd_smem<double>(tile, q1) : fd_smem<float>(tile, q1);
 }
 
-// Opt each variant into the dynamic shared memory it needs; once per process.
-// A variant that cannot fit on this device is refused (and the CUDA error
-// state cleared).
+// Opt each variant (both schemes' kernels) into the dynamic shared memory it
+// needs; once per process. A variant that cannot fit on this device is
+// refused (and the CUDA error state cleared).
 static cudaError_t fd_prepare(int precision, int tile, int q1) {
     static int state[2][FD_NTILES][3] = {};  // 0 unknown, 1 ready, 2 does not fit
     const int p = precision == LBM_FP64 ? 0 : 1;
@@ -581,22 +801,25 @@ static cudaError_t fd_prepare(int precision, int tile, int q1) {
         st = 2;
         return cudaErrorInvalidConfiguration;
     }
-    cudaError_t e = cudaFuncSetAttribute(fd_fn(precision, tile, q1), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)need);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        st = 2;
-        return cudaErrorInvalidConfiguration;
+    for (int scheme : {LBM_TS_RK3, LBM_TS_IMEX}) {
+        cudaError_t e = cudaFuncSetAttribute(fd_fn(precision, tile, q1, scheme),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = 2;
+            return cudaErrorInvalidConfiguration;
+        }
     }
     st = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_fd_stage(int precision, int q1, int tile, int grid, const GroupDev& g, int j, int stage,
-                            cudaStream_t s) {
-    if (tile < 0 || tile >= FD_NTILES || grid <= 0 || q1 < 3 || q1 > 5 || stage < 1 || stage > 3)
+cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int grid, const GroupDev& g, int j,
+                            int stage, cudaStream_t s) {
+    if (tile < 0 || tile >= FD_NTILES || grid <= 0 || q1 < 3 || q1 > 5 ||
+        (scheme != LBM_TS_RK3 && scheme != LBM_TS_IMEX) || stage < 1 || stage > fd_stages(scheme))
         return cudaErrorInvalidValue;
-    const void* fn = fd_fn(precision, tile, q1);
+    const void* fn = fd_fn(precision, tile, q1, scheme);
     cudaError_t e = fd_prepare(precision, tile, q1);
     if (e != cudaSuccess) return e;
     GroupDev gg = g;
@@ -612,7 +835,8 @@ bool fd_variant_fits(int precision, int q1, int tile) {
 int fd_blocks_per_sm(int precision, int q1, int tile) {
     if (!fd_variant_fits(precision, q1, tile)) return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile, q1), fd_tile_tx(tile) * fd_tile_ty(tile),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile, q1, LBM_TS_RK3),
+                                                      fd_tile_tx(tile) * fd_tile_ty(tile),
                                                       fd_bytes(precision, tile, q1)) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;

@@ -1,17 +1,26 @@
 // Continuous-batching run server.
 //
 // Requests are complete runs (model, lattice, tau, steps, initial state).
-// One worker thread owns a dynamic Engine: it admits queued requests as
-// slots and device memory (an HBM budget on the summed lattice footprints)
-// free up, advances every resident run together in rounds that give each
-// run about the same device time (the cheapest run advances chunk_steps
-// steps, costlier ones proportionally fewer; one captured CUDA-graph replay
-// per 32 steps, runs that have spent their allotment are skipped by the
-// kernels), and retires finished runs at the end of a round: final
-// observables, recorded series, fitted apparent viscosity, then the lattice's
-// memory is released and waiting requests are admitted.
-// Requests that arrive while others are on the GPU join at the next round,
-// so their work overlaps on the device.
+// Runs go to one of two lanes by their estimated step cost: small runs and
+// large runs (a step of a 2048^2 16-velocity FD lattice or more). Each lane
+// is a worker thread owning a dynamic Engine on its own CUDA stream, the
+// small-run lane's at the device's highest stream priority and the large-run
+// lane's at the lowest: both lanes' kernels run on the GPU at the same time,
+// the small runs' blocks are dispatched first as SMs free up (the large
+// lane launches many short blocks, so SMs free up every few tens of
+// microseconds), and the large runs use the rest, so a large run is not held
+// back by the rounds of the
+// small ones (nor they by its long steps). A lane admits queued requests of
+// its class as slots and device memory (an HBM budget on the summed lattice
+// footprints of both lanes) free up, advances its resident runs together in
+// rounds that give each run about the same device time (the cheapest run
+// advances its lane's chunk of steps, costlier ones proportionally fewer; one
+// captured CUDA-graph replay per 32 steps, runs that have spent their
+// allotment are skipped by the kernels), and retires finished runs at the end
+// of a round: final observables, recorded series, fitted apparent viscosity,
+// then the lattice's memory is released and waiting requests are admitted.
+// Requests that arrive while others are on the GPU join at their lane's next
+// round. With a caller's stream the server runs one lane on it.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -37,8 +46,10 @@ struct Req {
     long long left = 0;  // steps still to run (worker thread only)
     size_t bytes = 0;
     bool cancel = false;
+    int lane = 0;        // 0 small runs, 1 large runs
     lbm_result res{};
     std::vector<lbm_obs> series;
+    std::vector<double> rho, ux, uy;   // final fields (keep_moments)
 };
 
 // Initial fields of a request (Sec. 4.1-4.3 set-ups), node coordinates
@@ -93,28 +104,43 @@ void plan_round(const double* cost, const long long* left, size_t n, int chunk, 
     }
 }
 
+// Runs whose estimated step (step_cost) takes this long or longer go to the
+// large-run lane: FD 16-velocity FP32 from 2048^2 (~1 ms), CS FP32 from
+// about 6000^2.
+constexpr double kLargeStepCost = 0.5e-3;
+
+// A lane: a worker thread with its engine, its stream and its runs.
+struct Lane {
+    lbm::Engine e;
+    std::thread worker;
+    std::deque<uint64_t> queue;     // guarded by the server's mutex
+    std::vector<uint64_t> running;  // worker thread only
+    int inject_applied = 0;         // worker thread only
+    int chunk = 1;
+    cudaStream_t stream = nullptr;  // created by the server (null: the caller's stream)
+};
+
 }  // namespace
 
 struct lbm_server {
-    lbm::Engine e;
+    Lane lanes[2];
+    int n_lanes = 2;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::thread worker;
     bool stop = false;
     size_t budget = 0, resident = 0;
+    int resident_runs = 0;          // admitted and not finished, both lanes (guarded by mu)
     int max_slots = 1, chunk = 256;
     uint64_t next_ticket = 1;
     std::map<uint64_t, Req> reqs;
-    std::deque<uint64_t> queue;
-    std::vector<uint64_t> running;
     int64_t n_done = 0;
     std::atomic<int> inject_req{0};  // wait-timeout injection requested (microseconds, 0 = off)
-    int inject_applied = 0;          // worker thread only
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 
     void finish(Req& q, int status) {  // caller holds mu
+        if (q.state == 1) --resident_runs;
         q.state = 2;
         q.t_done = now();
         q.res.status = status;
@@ -125,10 +151,11 @@ struct lbm_server {
         q.res.n_series = (int64_t)q.series.size();
         ++n_done;
         cv_done.notify_all();
+        cv_work.notify_all();   // slots or memory may have freed up for the other lane
     }
 
-    // Set-up of an admitted request on the worker thread (no lock held).
-    int start(Req& q) {
+    // Set-up of an admitted request on its lane's worker thread (no lock held).
+    int start(lbm::Engine& e, Req& q) {
         int idx = -1;
         int rc = e.add_lattice(&q.r.spec, &idx);
         if (rc) return rc;
@@ -159,9 +186,17 @@ struct lbm_server {
     }
 
     // Results of a run whose budget is exhausted (worker thread, no lock).
-    int collect(Req& q) {
+    int collect(lbm::Engine& e, Req& q) {
         int rc = e.observables(q.lat, &q.res.last);
         if (rc) return rc;
+        if (q.r.keep_moments) {
+            const size_t n = (size_t)q.r.spec.nx * q.r.spec.ny;
+            q.rho.resize(n);
+            q.ux.resize(n);
+            q.uy.resize(n);
+            rc = e.moments(q.lat, q.rho.data(), q.ux.data(), q.uy.data());
+            if (rc) return rc;
+        }
         q.res.steps = e.L(q.lat).step0;
         if (q.r.obs_every > 0) {
             long long n = 0;
@@ -191,23 +226,28 @@ struct lbm_server {
         return q.res.last.nonfinite ? LBM_ENONFINITE : LBM_OK;
     }
 
-    void loop() {
+    void loop(int li) {
+        Lane& ln = lanes[li];
+        lbm::Engine& e = ln.e;
+        std::vector<uint64_t>& running = ln.running;
         for (;;) {
             std::vector<uint64_t> admit;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
                     // admission: oldest first, skipping requests that do not
-                    // fit yet (first fit over the queue)
-                    for (auto it = queue.begin(); it != queue.end();) {
+                    // fit yet (first fit over the lane's queue); slots and
+                    // memory are shared by the lanes
+                    for (auto it = ln.queue.begin(); it != ln.queue.end();) {
                         Req& q = reqs[*it];
-                        if ((int)(running.size() + admit.size()) >= max_slots) break;
+                        if (resident_runs >= max_slots) break;
                         if (resident + q.bytes <= budget) {
                             resident += q.bytes;
+                            ++resident_runs;
                             q.state = 1;
                             q.t_admit = now();
                             admit.push_back(*it);
-                            it = queue.erase(it);
+                            it = ln.queue.erase(it);
                         } else {
                             ++it;
                         }
@@ -223,7 +263,7 @@ struct lbm_server {
                     std::lock_guard<std::mutex> lk(mu);
                     q = &reqs[t];
                 }
-                const int rc = start(*q);
+                const int rc = start(e, *q);
                 std::lock_guard<std::mutex> lk(mu);
                 if (rc) {
                     if (q->lat >= 0) e.remove_lattice(q->lat);
@@ -236,9 +276,9 @@ struct lbm_server {
             if (running.empty()) continue;
             int rc = LBM_OK;
             const int want = inject_req.load();
-            if (want != inject_applied) {
+            if (want != ln.inject_applied) {
                 rc = e.inject_wait_timeout(want);
-                inject_applied = want;
+                ln.inject_applied = want;
             }
             // One round: every resident run gets about the same device time.
             // The cheapest run (by step_cost) advances `chunk` steps, a run
@@ -259,7 +299,7 @@ struct lbm_server {
                     cost[i] = step_cost(rq[i]->r.spec);
                     left[i] = rq[i]->left;
                 }
-                plan_round(cost.data(), left.data(), rq.size(), chunk, steps.data());
+                plan_round(cost.data(), left.data(), rq.size(), ln.chunk, steps.data());
                 std::vector<std::pair<int, long long>> budgets;
                 for (size_t i = 0; i < rq.size(); ++i) {
                     round_steps = std::max(round_steps, steps[i]);
@@ -284,7 +324,7 @@ struct lbm_server {
                     continue;
                 }
                 int st = rc;
-                if (st == LBM_OK && !cancel) st = collect(*q);
+                if (st == LBM_OK && !cancel) st = collect(e, *q);
                 else if (st == LBM_OK) st = LBM_ECANCELLED;
                 e.remove_lattice(q->lat);
                 std::lock_guard<std::mutex> lk(mu);
@@ -306,16 +346,42 @@ int lbm_server_create(lbm_server** out, size_t hbm_budget_bytes, int max_slots, 
         }
         *out = nullptr;
         lbm_server* s = new lbm_server;
-        s->e.dynamic_ = true;
-        const int rc = s->e.open(stream);
-        if (rc) {
-            delete s;
-            return rc;
-        }
         s->budget = hbm_budget_bytes;
         s->max_slots = max_slots;
         s->chunk = chunk_steps;
-        s->worker = std::thread([s] { s->loop(); });
+        s->n_lanes = stream ? 1 : 2;
+        int lo = 0, hi = 0;   // stream priorities: numerically lower is higher
+        cudaError_t e_streams = cudaSuccess;
+        if (!stream) {
+            cudaError_t& e = e_streams;
+            e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->lanes[0].stream, cudaStreamNonBlocking, hi);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->lanes[1].stream, cudaStreamNonBlocking, lo);
+        }
+        // on failure: the engines go first (they finish their streams), then the streams
+        auto fail = [s](int rc) {
+            cudaStream_t st[2] = {s->lanes[0].stream, s->lanes[1].stream};
+            delete s;
+            for (cudaStream_t x : st)
+                if (x) cudaStreamDestroy(x);
+            return rc;
+        };
+        if (e_streams != cudaSuccess) return fail(lbm::cuda_fail(e_streams, "server streams"));
+        for (int li = 0; li < s->n_lanes; ++li) {
+            Lane& ln = s->lanes[li];
+            ln.e.dynamic_ = true;
+            ln.chunk = li == 0 ? chunk_steps : std::max(1, chunk_steps / 8);
+            // Blocks of a running kernel are not preempted: stream priority
+            // only decides which stream's blocks fill SMs as they free up. A
+            // large lane of one block set per SM holds every SM for a whole
+            // launch (an FD 4096^2 stage: 1.1 ms) and the small lane waits
+            // that long for each of its steps; with 16 block sets, each
+            // block covers a few tiles (about 70 us of that stage).
+            if (li == 1) ln.e.grid_mult_ = 16;
+            const int rc = ln.e.open(stream ? stream : ln.stream);
+            if (rc) return fail(rc);
+        }
+        for (int li = 0; li < s->n_lanes; ++li) s->lanes[li].worker = std::thread([s, li] { s->loop(li); });
         *out = s;
         return LBM_OK;
     } catch (...) {
@@ -347,9 +413,10 @@ int lbm_submit(lbm_server* s, const lbm_request* req, uint64_t* ticket) {
         q.r.spec = spec;
         q.bytes = bytes;
         q.t_submit = s->now();
-        s->queue.push_back(t);
+        q.lane = (s->n_lanes > 1 && step_cost(spec) >= kLargeStepCost) ? 1 : 0;
+        s->lanes[q.lane].queue.push_back(t);
         *ticket = t;
-        s->cv_work.notify_one();
+        s->cv_work.notify_all();
         return LBM_OK;
     } catch (...) {
         lbm::set_error("submit failed");
@@ -379,6 +446,35 @@ int lbm_result_series(lbm_server* s, uint64_t ticket, lbm_obs* out, int64_t cap,
     return LBM_OK;
 }
 
+int lbm_result_moments(lbm_server* s, uint64_t ticket, double* rho, double* ux, double* uy) {
+    if (!s || !rho || !ux || !uy) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return LBM_ENOTFOUND;
+    const Req& q = it->second;
+    if (q.state != 2) return LBM_ENOTREADY;
+    const size_t n = (size_t)q.r.spec.nx * q.r.spec.ny;
+    if (q.rho.size() != n) {
+        lbm::set_error("no kept fields for this ticket (request without keep_moments, or the run failed)");
+        return LBM_ENOTFOUND;
+    }
+    std::copy(q.rho.begin(), q.rho.end(), rho);
+    std::copy(q.ux.begin(), q.ux.end(), ux);
+    std::copy(q.uy.begin(), q.uy.end(), uy);
+    return LBM_OK;
+}
+
+int lbm_release(lbm_server* s, uint64_t ticket) {
+    if (!s) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return LBM_ENOTFOUND;
+    if (it->second.state != 2) return LBM_ENOTREADY;
+    s->reqs.erase(it);
+    --s->n_done;   // finished results still held
+    return LBM_OK;
+}
+
 int lbm_cancel(lbm_server* s, uint64_t ticket) {
     if (!s) return LBM_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -386,9 +482,10 @@ int lbm_cancel(lbm_server* s, uint64_t ticket) {
     if (it == s->reqs.end()) return LBM_ENOTFOUND;
     Req& q = it->second;
     if (q.state == 0) {
-        for (auto qi = s->queue.begin(); qi != s->queue.end(); ++qi)
+        auto& queue = s->lanes[q.lane].queue;
+        for (auto qi = queue.begin(); qi != queue.end(); ++qi)
             if (*qi == ticket) {
-                s->queue.erase(qi);
+                queue.erase(qi);
                 break;
             }
         s->finish(q, LBM_ECANCELLED);
@@ -451,8 +548,9 @@ int lbm_server_drain(lbm_server* s, double timeout_s) {
 int lbm_server_stats(lbm_server* s, int64_t* queued, int64_t* running, int64_t* finished, size_t* resident_bytes) {
     if (!s) return LBM_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    if (queued) *queued = (int64_t)s->queue.size();
-    if (running) *running = (int64_t)s->reqs.size() - (int64_t)s->queue.size() - s->n_done;
+    const int64_t nq = (int64_t)(s->lanes[0].queue.size() + s->lanes[1].queue.size());
+    if (queued) *queued = nq;
+    if (running) *running = (int64_t)s->reqs.size() - nq - s->n_done;
     if (finished) *finished = s->n_done;
     if (resident_bytes) *resident_bytes = s->resident;
     return LBM_OK;
@@ -463,12 +561,18 @@ void lbm_server_destroy(lbm_server* s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
-        for (uint64_t t : s->queue) s->finish(s->reqs[t], LBM_ECANCELLED);
-        s->queue.clear();
+        for (auto& ln : s->lanes) {
+            for (uint64_t t : ln.queue) s->finish(s->reqs[t], LBM_ECANCELLED);
+            ln.queue.clear();
+        }
         s->cv_work.notify_all();
     }
-    if (s->worker.joinable()) s->worker.join();
-    delete s;
+    for (auto& ln : s->lanes)
+        if (ln.worker.joinable()) ln.worker.join();
+    cudaStream_t streams[2] = {s->lanes[0].stream, s->lanes[1].stream};
+    delete s;   // the engines finish and release their work first
+    for (cudaStream_t st : streams)
+        if (st) cudaStreamDestroy(st);
 }
 
 }  // extern "C"

@@ -38,7 +38,8 @@ class lbm_obs(ctypes.Structure):
 class lbm_spec(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("q_per_axis", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("precision", ctypes.c_int), ("storage", ctypes.c_int), ("tau", ctypes.c_double),
-                ("dt", ctypes.c_double), ("dx", ctypes.c_double), ("rho0", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("dx", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("scheme", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class lbm_view(ctypes.Structure):
@@ -48,6 +49,7 @@ class lbm_view(ctypes.Structure):
 
 class lbm_request(ctypes.Structure):
     _fields_ = [("spec", lbm_spec), ("steps", ctypes.c_int64), ("init", ctypes.c_int), ("obs_every", ctypes.c_int),
+                ("keep_moments", ctypes.c_int), ("reserved", ctypes.c_int),
                 ("U", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_r", ctypes.c_double),
                 ("user_tag", ctypes.c_uint64)]
 
@@ -143,6 +145,9 @@ _SIGS = [
     ("lbm_poll", _i, [_P, ctypes.c_uint64, ctypes.POINTER(lbm_result)]),
     ("lbm_result_series", _i, [_P, ctypes.c_uint64, ctypes.POINTER(lbm_obs), _i64, ctypes.POINTER(_i64)]),
     ("lbm_cancel", _i, [_P, ctypes.c_uint64]),
+    ("lbm_probe_fp32", _i, [_i, _D, ctypes.POINTER(_i), _D]),
+    ("lbm_result_moments", _i, [_P, ctypes.c_uint64, _D, _D, _D]),
+    ("lbm_release", _i, [_P, ctypes.c_uint64]),
     ("lbm_server_drain", _i, [_P, _d]),
     ("lbm_server_stats", _i, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                               ctypes.POINTER(_sz)]),
@@ -237,19 +242,32 @@ def lbm_fit_decay(t, a, t_skip=0.0):
     return g.value, a0.value
 
 
+def probe_fp32(packed=True):
+    """Measured FP32 rate of the current device (lbm_probe_fp32): (flops/s,
+    SM count, ms per probe launch)."""
+    f, n, ms = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    check(lib().lbm_probe_fp32(1 if packed else 0, ctypes.byref(f), ctypes.byref(n), ctypes.byref(ms)),
+          "lbm_probe_fp32")
+    return f.value, n.value, ms.value
+
+
 MODELS = {"cs": LBM_CS, "fd": LBM_FD}
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp32dev": LBM_FP32_DEV}
 LBM_STORE_AB, LBM_STORE_INPLACE = 0, 1
 STORAGES = {"ab": LBM_STORE_AB, "inplace": LBM_STORE_INPLACE}
+LBM_TS_RK3, LBM_TS_IMEX = 0, 1
+SCHEMES = {"rk3": LBM_TS_RK3, "imex": LBM_TS_IMEX}
 
 
-def make_spec(model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, storage="ab") -> lbm_spec:
+def make_spec(model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, storage="ab",
+              scheme="rk3") -> lbm_spec:
     s = lbm_spec()
     s.model = MODELS[model] if isinstance(model, str) else model
     s.q_per_axis = q
     s.nx, s.ny = nx, ny
     s.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
     s.storage = STORAGES[storage] if isinstance(storage, str) else storage
+    s.scheme = SCHEMES[scheme] if isinstance(scheme, str) else scheme
     s.tau, s.dt, s.dx, s.rho0 = tau, dt, dx, rho0
     return s
 
@@ -263,10 +281,10 @@ def _stream_ptr(stream):
 
 
 def spec_from_nu(model, q, nx, ny, nu, nu_model=None, n_ref=0, dt=0.0, dx=0.0, precision="fp64", rho0=0.0,
-                 storage="ab") -> lbm_spec:
+                 storage="ab", scheme="rk3") -> lbm_spec:
     """lbm_spec_from_nu: the resolved spec of a lattice given its viscosity
     (in the units of nu_model, default the lattice's own model)."""
-    s = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage)
+    s = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage, scheme)
     nm = s.model if nu_model is None else (MODELS[nu_model] if isinstance(nu_model, str) else nu_model)
     out = lbm_spec()
     check(lib().lbm_spec_from_nu(ctypes.byref(s), nu, nm, n_ref, ctypes.byref(out)), "lbm_spec_from_nu")
@@ -278,15 +296,15 @@ class Lattice:
     of tau (tau=None) the context is made by lbm_create_nu."""
 
     def __init__(self, model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, stream=None, storage="ab",
-                 nu=None, nu_model=None, n_ref=0):
+                 nu=None, nu_model=None, n_ref=0, scheme="rk3"):
         self._h = ctypes.c_void_p()
         if tau is None:
-            spec = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage)
+            spec = make_spec(model, q, nx, ny, 0.0, dt, dx, precision, rho0, storage, scheme)
             nm = spec.model if nu_model is None else (MODELS[nu_model] if isinstance(nu_model, str) else nu_model)
             check(lib().lbm_create_nu(ctypes.byref(self._h), ctypes.byref(spec), nu, nm, n_ref,
                                       _stream_ptr(stream)), "lbm_create_nu")
         else:
-            spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0, storage)
+            spec = make_spec(model, q, nx, ny, tau, dt, dx, precision, rho0, storage, scheme)
             check(lib().lbm_create_spec(ctypes.byref(self._h), ctypes.byref(spec), _stream_ptr(stream)),
                   "lbm_create")
         out = lbm_spec()
@@ -521,12 +539,14 @@ class Batch:
 INITS = {"tg": 0, "taylor_green": 0, "shear": 1, "shock": 2}
 
 
-def make_request(spec: lbm_spec, steps, init="tg", U=0.01, obs_every=0, rho_l=1.1, rho_r=0.9, tag=0) -> lbm_request:
+def make_request(spec: lbm_spec, steps, init="tg", U=0.01, obs_every=0, rho_l=1.1, rho_r=0.9, tag=0,
+                 keep_moments=False) -> lbm_request:
     r = lbm_request()
     r.spec = spec
     r.steps = int(steps)
     r.init = INITS[init] if isinstance(init, str) else init
     r.obs_every = int(obs_every)
+    r.keep_moments = 1 if keep_moments else 0
     r.U, r.rho_l, r.rho_r = U, rho_l, rho_r
     r.user_tag = tag
     return r
@@ -586,6 +606,15 @@ class Server:
         arr = (lbm_obs * max(n.value, 1))()
         check(lib().lbm_result_series(self._h, ticket, arr, n.value, ctypes.byref(n)), "lbm_result_series")
         return [arr[i].as_dict() for i in range(n.value)]
+
+    def moments(self, ticket, nx, ny):
+        """Kept final fields of a finished run (lbm_result_moments)."""
+        r, u, v = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx))
+        check(lib().lbm_result_moments(self._h, ticket, _dp(r), _dp(u), _dp(v)), "lbm_result_moments")
+        return r, u, v
+
+    def release(self, ticket):
+        check(lib().lbm_release(self._h, ticket), "lbm_release")
 
     def cancel(self, ticket):
         check(lib().lbm_cancel(self._h, ticket), "lbm_cancel")

@@ -235,3 +235,29 @@ def test_spec_from_nu_validation(args, code):
     with pytest.raises(lbm.LbmError) as ei:
         pkg.Lattice(a.pop("model"), a.pop("q"), a.pop("nx"), a.pop("ny"), None, **a)
     assert ei.value.code == code
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(model="fd", q=4, tau=1e-4, dt=1e-3, scheme="rk3"), lbm.LBM_ESTIFF),   # RK3 needs dt <= tau
+    (dict(model="cs", q=3, tau=0.5, dt=0.0, scheme="imex"), lbm.LBM_EINVAL),    # the scheme is an FD choice
+    (dict(model="fd", q=4, tau=1e-4, dt=1e-3, scheme=7), lbm.LBM_EINVAL),
+    (dict(model="fd", q=4, tau=1e-4, dt=2e-2, scheme="imex"), lbm.LBM_ECFL),    # IMEX keeps the CFL bound
+])
+def test_scheme_validation(kw, code):
+    """IMEX lifts dt <= tau (Sec. 4.1) and nothing else; the RK3 default
+    keeps it (checked on the host before any device work)."""
+    s = pkg.make_spec(kw["model"], kw["q"], 32, 32, kw["tau"], kw["dt"], 0.0, "fp64", scheme=kw["scheme"])
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Batch([s])
+    assert ei.value.code == code
+    s = pkg.make_spec("fd", 4, 32, 32, 1e-4, 1e-3, 0.0, "fp64", scheme="imex")
+    s.reserved = 1
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.Batch([s])
+    assert ei.value.code == lbm.LBM_EINVAL
+    # an IMEX lattice with dt = 10 tau passes validation (spec_from_nu only resolves)
+    ok = pkg.spec_from_nu("fd", 4, 32, 32, 1e-4, "fd", dt=1e-3, precision="fp32", scheme="imex")
+    assert ok.scheme == lbm.LBM_TS_IMEX and ok.tau == 1e-4
+    with pytest.raises(lbm.LbmError) as ei:
+        pkg.spec_from_nu("fd", 4, 32, 32, 1e-4, "fd", dt=1e-3, precision="fp32")
+    assert ei.value.code == lbm.LBM_ESTIFF

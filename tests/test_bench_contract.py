@@ -9,17 +9,22 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(env_extra):
+def _run(env_extra, wall=None):
+    import time
     env = dict(os.environ, **env_extra)
+    t0 = time.perf_counter()
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "3", "--cpu-budget", "0.3"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
+    if wall is not None:
+        wall.append(time.perf_counter() - t0)
     assert r.returncode == 0, r.stderr[-2000:]
     return [ln for ln in r.stdout.splitlines() if ln.strip()]
 
 
 def test_reference_arm_prints_one_contract_line():
-    lines = _run({})
+    wall = []
+    lines = _run({}, wall)
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference"
@@ -32,6 +37,10 @@ def test_reference_arm_prints_one_contract_line():
     cb = rec["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == rec["value"] and cb["sample"]
     assert rec["e2e"] == {"value": rec["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the line reports what it ran: its own step time fits inside the run,
+    # and the extrapolation to the workload mix is stated
+    assert 0 < rec["ms_per_step"] * (rec["steps"] + rec["warmup"]) / 1e3 <= wall[0]
+    assert rec["config"]["ran"] and "extrapolated" in rec["config"]["value_is"]
 
 
 def test_reference_arm_other_ranks_print_nothing():

@@ -164,3 +164,49 @@ def test_cheap_run_is_not_held_to_the_pace_of_an_expensive_one():
     assert rl["status"] == rs["status"] == lbm.LBM_OK
     assert rl["steps"] == 300 and rs["steps"] == 1000
     assert rs["t_done"] < rl["t_done"], (rs["t_done"], rl["t_done"])
+
+
+def test_kept_moments_and_release():
+    """A run submitted with keep_moments returns its final rho, u fields, the
+    same as the lattice computes alone; releasing a finished ticket frees its
+    result, series and fields (later calls: LBM_ENOTFOUND) and drops it from
+    the finished count, while a running ticket cannot be released."""
+    import numpy as np
+    import lbm_workloads as wl
+    spec = _cs(64, 0.5)
+    U = 0.01 * SQ3
+    with lbm.Server(8 * GB, 8, 32) as S:
+        t_keep = S.submit(lbm.make_request(spec, 300, "tg", U, obs_every=10, keep_moments=True))
+        t_plain = S.submit(lbm.make_request(spec, 300, "tg", U, obs_every=10))
+        t_long = S.submit(lbm.make_request(_cs(512, 0.6), 200000, "tg", 0.01))
+        while S.poll(t_keep) is None or S.poll(t_plain) is None:
+            time.sleep(0.01)
+        with pytest.raises(lbm.LbmError) as ei:
+            S.release(t_long)               # still running
+        assert ei.value.code == lbm.LBM_ENOTREADY
+        rho, ux, uy = S.moments(t_keep, 64, 64)
+        with pytest.raises(lbm.LbmError) as ei:
+            S.moments(t_plain, 64, 64)       # not kept
+        assert ei.value.code == lbm.LBM_ENOTFOUND
+        assert len(S.series(t_keep)) == 30
+        before = S.stats()["finished"]
+        S.release(t_keep)
+        assert S.stats()["finished"] == before - 1
+        for call in (lambda: S.poll(t_keep), lambda: S.series(t_keep), lambda: S.moments(t_keep, 64, 64),
+                     lambda: S.release(t_keep)):
+            with pytest.raises(lbm.LbmError) as ei:
+                call()
+            assert ei.value.code == lbm.LBM_ENOTFOUND
+        S.cancel(t_long)
+        S.drain(120)                         # released tickets do not hold the drain
+        S.release(t_plain)
+        S.release(t_long)
+        assert S.stats()["finished"] == 0
+    with pkg.Lattice("cs", 3, 64, 64, 0.5, precision="fp32", storage="ab") as L:
+        L.init(*wl.taylor_green(64, 64, U))
+        L.step(300)
+        r2, u2, v2 = L.moments()
+    # the server forms the initial fields itself (libm sin/cos; the test uses
+    # numpy's), so the two FP32 runs may differ by a float rounding
+    assert np.max(np.abs(rho - r2)) < 1e-6
+    assert np.max(np.abs(ux - u2)) < 1e-5 * U and np.max(np.abs(uy - v2)) < 1e-5 * U
