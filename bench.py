@@ -19,7 +19,9 @@ decay-rate errors); the served leg (a Poisson stream of CS / FD runs of
 64^2..4096^2 nodes and 1k..20k steps into the continuous-batching server:
 p50/p99 latency and slowdown, aggregate rate, FP32 errors of every run up to
 256^2 against FP64); the IMEX leg (FD 16-velocity 4096^2 with tau below the
-Courant-limited step: RK3 at dt = tau against IMEX at the Courant limit);
+Courant-limited step: RK3 at dt = tau against IMEX at the Courant limit); the
+fused leg (FD 16-velocity 4096^2, the temporally blocked RK3 step against the
+three stage launches);
 and the FP64 oracle's rate on every host core (cpu_baseline).
 
 --impl reference times the FP64 C oracle on the host cores instead (the
@@ -369,6 +371,7 @@ def run_gpu(args, rank, world):
     if not args.no_extras:
         rec["batched"] = run_batched(torch)
         rec["imex"] = run_imex(torch)
+        rec["fused"] = run_fused(torch)
         rec["served"] = run_served(torch, n_req=args.served_requests, load=args.served_load[0],
                                    chunk=args.served_chunk)
     if rates is not None:
@@ -698,6 +701,39 @@ def run_imex(torch, n=FD_N, tau=1e-5, steps=24, warm=3):
     return out
 
 
+def run_fused(torch, n=FD_N, steps=20, warm=3):
+    """FD 16-velocity FP32 on an n^2 Taylor-Green lattice (tau = 5e-4, dt =
+    1e-5, the roofline configuration): the temporally blocked SSP-RK3 step
+    (one launch per step, 2Q values of device memory per update) against the
+    three stage launches (8Q values). CUDA-event times per launch. The fused
+    kernel also evaluates stages 1 and 2 on the halo of every tile (6.5
+    node-stages per updated node for 32 x 8 tiles against 3), so its
+    arithmetic per update is 2.2x larger while its bytes are 4x smaller."""
+    import paper_1904_02471_gb300 as pkg
+    out = {"lattice": [n, n], "velocities": 16, "tau_fd": FD_TAU, "dt_fd": FD_DT, "precision": "fp32",
+           "steps": steps}
+    for scheme in ("rk3", "rk3_fused"):
+        spec = pkg.make_spec("fd", 4, n, n, FD_TAU, FD_DT, 0.0, "fp32", scheme=scheme)
+        B = pkg.Batch([spec])
+        B.init(0, *wl.taylor_green(n, n, U0))
+        B.record(0, steps, 4)
+        B.step_profiled(warm)
+        ms, total = B.step_profiled(steps)
+        ser = B.series(0)
+        B.close()
+        nst = 1 if scheme == "rk3_fused" else 3
+        stage = [float(ms[0][k]) / steps for k in range(nst)]
+        step_ms = sum(stage)
+        bytes_lu = (2 if scheme == "rk3_fused" else 8) * 16 * 4
+        out[scheme] = {"launches_per_step": nst, "launch_ms": [round(x, 4) for x in stage],
+                       "ms_per_step": round(step_ms, 4), "mlups": round(n * n / (step_ms / 1e3) / 1e6, 1),
+                       "gbs": round(n * n * bytes_lu / (step_ms / 1e3) / 1e9, 1), "bytes_per_lu": bytes_lu,
+                       "frac_hbm": round(n * n * bytes_lu / (step_ms / 1e3) / 1e9 / peaks()[0], 4),
+                       "finite": all(x["nonfinite"] == 0 for x in ser)}
+    out["fused_over_rk3"] = round(out["rk3_fused"]["mlups"] / out["rk3"]["mlups"], 3)
+    return out
+
+
 def run_served_full(torch, n_req, loads, seed=0, chunk=128):
     """The served stream at several loads (one record)."""
     sides = SERVED_SIDES
@@ -836,7 +872,8 @@ def main():
     ap.add_argument("--q", type=int, default=4, help="--profile-case fd: nodes per axis")
     ap.add_argument("--precision", default="fp32", help="--profile-case: fp32 or fp64")
     ap.add_argument("--storage", default="ab", choices=["ab", "inplace"], help="--profile-case cs: storage")
-    ap.add_argument("--scheme", default="rk3", choices=["rk3", "imex"], help="--profile-case fd: time scheme")
+    ap.add_argument("--scheme", default="rk3", choices=["rk3", "imex", "rk3_fused"],
+                    help="--profile-case fd: time scheme")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

@@ -88,8 +88,8 @@ typedef struct {
  * LBM_STORE_INPLACE: one buffer updated in place (the AA access pattern:
  * even steps collide at the node and write to the opposite velocity's slot,
  * odd steps read and write the nine locations a node owns), half the device
- * memory at the same traffic and bit-identical results. FD needs its three
- * stage buffers: LBM_STORE_INPLACE with LBM_FD is LBM_EINVAL. */
+ * memory at the same traffic and bit-identical results. FD needs its stage
+ * buffers: LBM_STORE_INPLACE with LBM_FD is LBM_EINVAL. */
 #define LBM_STORE_AB 0
 #define LBM_STORE_INPLACE 1
 
@@ -103,6 +103,16 @@ typedef struct {
  * lattice takes LBM_TS_RK3 (the field is ignored there and must be 0). */
 #define LBM_TS_RK3 0
 #define LBM_TS_IMEX 1
+/* LBM_TS_RK3_FUSED: the SSP-RK3 step of LBM_TS_RK3 (same stages, same
+ * dt <= tau) temporally blocked: the three stages of a step in one launch per
+ * tile (the stages of Sec. 2, not a different scheme). A tile reads f^n
+ * with a halo of 9 nodes, computes stage 1 on the tile plus 6 nodes and
+ * stage 2 on the tile plus 3 nodes in shared memory, and writes only
+ * f^(n+1): 2Q values of device memory per lattice update instead of 8Q, and
+ * two state buffers instead of three, for 2.2x the stage evaluations of the
+ * three stage launches (the halo nodes). Results equal LBM_TS_RK3's to
+ * rounding (the same arithmetic per node and stage). FD only. */
+#define LBM_TS_RK3_FUSED 2
 
 /* Parameters of a lattice. See lbm_create for their meaning. */
 typedef struct {
@@ -115,7 +125,7 @@ typedef struct {
     double dt;        /* time step (CS: 0 selects 1/sqrt(3)) */
     double dx;        /* node spacing (CS: 0 selects 1; FD: 0 selects 1/nx) */
     double rho0;      /* reference density of the FP32 deviation storage (0 selects 1) */
-    int scheme;       /* FD time integration: LBM_TS_RK3 (0, default) or LBM_TS_IMEX */
+    int scheme;       /* FD time integration: LBM_TS_RK3 (0, default), LBM_TS_IMEX or LBM_TS_RK3_FUSED */
     int reserved;     /* 0 */
 } lbm_spec;
 
@@ -166,7 +176,7 @@ int lbm_fit_decay(const double* t, const double* a, int64_t n, double t_skip, do
  *  cuda_stream: a cudaStream_t to enqueue work on, or NULL for a stream the
  *      library creates (the legacy default stream is never used).
  * Errors: LBM_EINVAL (bad sizes, model/q pair, tau <= dt/2 for CS, dx/dt),
- *  LBM_ECFL (max|v_ka| dt/dx > 1), LBM_ESTIFF (FD dt > tau with the RK3
+ *  LBM_ECFL (max|v_ka| dt/dx > 1), LBM_ESTIFF (FD dt > tau with an RK3
  *  scheme), LBM_ENOMEM, LBM_ECUDA. On error *out is NULL. The state is zero
  *  until lbm_init. lbm_create makes RK3 lattices; lbm_create_spec takes the
  *  scheme from the spec. */
@@ -222,7 +232,8 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f);
 
 /* Enqueue n >= 0 time steps on the context stream and return. One step is
  * one application of Eq. (sc_evolution) (CS) or one RK step of the lattice's
- * scheme (FD: three stages, or two with LBM_TS_IMEX). */
+ * scheme (FD: three stages, two with LBM_TS_IMEX; LBM_TS_RK3_FUSED runs the
+ * three stages in one launch). */
 int lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Wait for all enqueued work. Returns LBM_ECUDA if a kernel failed. */

@@ -48,7 +48,7 @@ def _digest(extra=()) -> str:
 
 
 KERNEL_SOURCES = {
-    "fd_stage": ["kernels_fd.cu"],
+    "fd_stage": ["kernels_fd.cu", "fd_common.cuh"],
     "cs_bulk": ["kernels_cs.cu"],
 }
 SHARED_SOURCES = ["common.cuh", "ptx.cuh", "kernels.h"]

@@ -76,7 +76,7 @@ int Engine::tune(int trial_steps, std::string* report) {
         const int orig_any_obs = g.any_obs;
         g.any_obs = false;
         for (int t = 0; t < ntiles; ++t) {
-            if (g.model == LBM_FD && !fd_variant_fits(g.precision, g.q1, t)) continue;
+            if (g.model == LBM_FD && !fd_variant_fits(g.precision, g.q1, t, g.scheme)) continue;
             int rc = set_group_config(gi, t, 0);
             if (rc) return rc;
             g.any_obs = false;

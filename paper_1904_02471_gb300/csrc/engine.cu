@@ -101,8 +101,11 @@ int Engine::validate(const lbm_spec* in, lbm_spec* out) {
             set_error(b);
             return LBM_ECFL;
         }
-        if (s.scheme != LBM_TS_RK3 && s.scheme != LBM_TS_IMEX) { set_error("bad FD scheme"); return LBM_EINVAL; }
-        if (s.scheme == LBM_TS_RK3 && s.dt > s.tau * (1.0 + 1e-12)) {
+        if (s.scheme != LBM_TS_RK3 && s.scheme != LBM_TS_IMEX && s.scheme != LBM_TS_RK3_FUSED) {
+            set_error("bad FD scheme");
+            return LBM_EINVAL;
+        }
+        if (s.scheme != LBM_TS_IMEX && s.dt > s.tau * (1.0 + 1e-12)) {
             set_error("FD requires dt <= tau with the RK3 scheme (non-stiff BGK term, Sec. 4.1); "
                       "LBM_TS_IMEX lifts it");
             return LBM_ESTIFF;
@@ -147,7 +150,8 @@ void Engine::invalidate_graph() {
 // the items), or grid_mult_ block sets, so that each block covers fewer items
 // and retires sooner (SMs then free up for another stream's kernels).
 int Engine::persistent_grid(const Group& g, int tile) const {
-    int bps = g.model == LBM_CS ? cs_blocks_per_sm(g.precision, tile) : fd_blocks_per_sm(g.precision, g.q1, tile);
+    int bps = g.model == LBM_CS ? cs_blocks_per_sm(g.precision, tile)
+                                : fd_blocks_per_sm(g.precision, g.q1, tile, g.scheme);
     return (int)std::max<long long>(1, (long long)sm_count_ * bps);
 }
 
@@ -191,7 +195,7 @@ size_t Engine::footprint(const lbm_spec& s) {
     const int K = s.q_per_axis * s.q_per_axis;
     const long long pitch = (s.nx + 8 + 31) / 32 * 32;
     const long long plane = pitch * s.ny;
-    const int nbuf = s.model == LBM_CS ? (s.storage == LBM_STORE_INPLACE ? 1 : 2) : 3;
+    const int nbuf = state_buffers(s);
     const int elem = s.precision == LBM_FP64 ? 8 : 4;
     return (size_t)nbuf * (K * plane + Lattice::TAIL) * elem + sizeof(double) * NOBS * 1024;
 }
@@ -205,7 +209,7 @@ int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
     L.elem = s.precision == LBM_FP64 ? 8 : 4;
     L.pitch = (s.nx + 8 + 31) / 32 * 32;
     L.plane = (long long)L.pitch * s.ny;
-    L.nbuf = s.model == LBM_CS ? (s.storage == LBM_STORE_INPLACE ? 1 : 2) : 3;
+    L.nbuf = state_buffers(s);
     L.rho0s = s.precision == LBM_FP64 ? 0.0 : s.rho0;
     if (s.model == LBM_CS) {
         L.omega = s.dt / s.tau;
@@ -244,6 +248,9 @@ int Engine::add_lattice(const lbm_spec* spec, int* index, bool upload) {
         g.precision = s.precision;
         g.scheme = s.scheme;
         g.tile = s.model == LBM_CS ? (int)CS_B256x32 : (int)FD_T32x8;
+        // the fused FD kernel's largest tiles do not fit every set and precision
+        if (s.model == LBM_FD && s.scheme == LBM_TS_RK3_FUSED && !fd_variant_fits(s.precision, s.q_per_axis, g.tile, s.scheme))
+            g.tile = FD_T32x4;
         groups.push_back(g);
         gi = (int)groups.size() - 1;
         invalidate_graph();
@@ -423,7 +430,7 @@ int Engine::set_group_config(int gi, int tile, int grid) {
         set_error("no such tile variant");
         return LBM_EINVAL;
     }
-    if (g.model == LBM_FD && !fd_variant_fits(g.precision, g.q1, tile)) {
+    if (g.model == LBM_FD && !fd_variant_fits(g.precision, g.q1, tile, g.scheme)) {
         set_error("this FD tile variant needs more shared memory than the device offers for this set/precision");
         return LBM_EINVAL;
     }
@@ -469,7 +476,7 @@ int Engine::enqueue_chunk(int c) {
     }
     for (auto& g : groups) {
         if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
-        cudaError_t e = launch_advance(g.dev(), g.cap_lat, c, g.model == LBM_CS ? 1 : 0, stream_);
+        cudaError_t e = launch_advance(g.dev(), g.cap_lat, c, g.flips() ? 1 : 0, stream_);
         if (e != cudaSuccess) return cuda_fail(e, "launch_advance");
         ++n;
     }
@@ -483,7 +490,7 @@ void Engine::mirror_advance(int c) {
         const long long adv = std::min<long long>(L.remaining, c);
         L.step0 += adv;
         L.remaining -= adv;
-        if (L.spec.model == LBM_CS && (adv & 1)) L.cur ^= 1;
+        if (L.flips() && (adv & 1)) L.cur ^= 1;
     }
 }
 
@@ -581,7 +588,7 @@ int Engine::step_profiled(long long n, double* ms, int cap, double* total_ms) {
         }
         for (auto& g : groups) {
             if (g.cap_lat == 0) continue;  // empty groups launch too: kernels read the live count
-            cudaError_t e = launch_advance(g.dev(), g.cap_lat, 1, g.model == LBM_CS ? 1 : 0, stream_);
+            cudaError_t e = launch_advance(g.dev(), g.cap_lat, 1, g.flips() ? 1 : 0, stream_);
             if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "launch_advance"); }
             ++launches_;
         }

@@ -22,23 +22,34 @@ void set_error(const char* msg);
 inline void set_error(const std::string& msg) { set_error(msg.c_str()); }
 int cuda_fail(cudaError_t e, const char* what);
 
+// State buffers of a lattice: two-buffer CS 2, in-place CS 1, FD 3 (f^n and
+// the two stage buffers; IMEX: f^n, Z, P), temporally blocked FD 2 (f^n and
+// f^(n+1), alternating).
+inline int state_buffers(const lbm_spec& s) {
+    if (s.model == LBM_CS) return s.storage == LBM_STORE_INPLACE ? 1 : 2;
+    return s.scheme == LBM_TS_RK3_FUSED ? 2 : 3;
+}
+
 struct Lattice {
     lbm_spec spec{};
     int K = 0;
     int pitch = 0;
     long long plane = 0;
     int elem = 0;            // bytes per stored value
-    int nbuf = 0;            // 2 (CS) or 3 (FD)
+    int nbuf = 0;            // state buffers: state_buffers(spec)
     void* mem = nullptr;     // one allocation for all state buffers
     void* buf[3] = {nullptr, nullptr, nullptr};
     double omega = 0, cdx = 0, dt_tau = 0, rho0s = 0, eps = 1e-6;
     // host mirror of the device-side dynamic state
     long long step0 = 0;
     long long remaining = UNLIMITED;
-    int cur = 0;             // CS: buffer holding the state (two buffers) or phase (in place)
+    int cur = 0;             // buffer holding the state (two-buffer CS, fused FD; 0 for
+                             // RK3 / IMEX FD) or phase (in-place CS)
     bool inplace() const { return spec.model == LBM_CS && spec.storage == LBM_STORE_INPLACE; }
+    // cur flips with every step
+    bool flips() const { return spec.model == LBM_CS || spec.scheme == LBM_TS_RK3_FUSED; }
     // buffer that holds the current state
-    int state_buf() const { return spec.model == LBM_CS && !inplace() ? cur : 0; }
+    int state_buf() const { return inplace() ? 0 : cur; }
     // lbm_view::cs_pull_phase of the current state
     int phase_code() const { return spec.model != LBM_CS ? 0 : (!inplace() ? 1 : (cur ? 2 : 0)); }
     // observables
@@ -70,6 +81,8 @@ struct Lattice {
 struct Group {
     int model = 0, q1 = 0, precision = 0;
     int scheme = LBM_TS_RK3;   // FD time integration
+    // the lattices' cur flips with every step (CS, fused FD)
+    bool flips() const { return model == LBM_CS || scheme == LBM_TS_RK3_FUSED; }
     int tile = 0;
     int grid = 0;
     std::vector<int> members;

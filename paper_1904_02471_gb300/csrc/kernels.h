@@ -30,17 +30,24 @@ int fd_tile_ty(int v);
 // One CS step (Eq. sc_evolution) for every lattice of the group at sub-step j.
 cudaError_t launch_cs_step(int precision, int tile, int grid, const GroupDev& g, int j, cudaStream_t s);
 // One stage of the FD update for every lattice of the group: scheme
-// LBM_TS_RK3, SSP-RK3 stages 1..3; LBM_TS_IMEX, IMEX-SSP2(2,2,2) stages 1..2.
+// LBM_TS_RK3, SSP-RK3 stages 1..3; LBM_TS_IMEX, IMEX-SSP2(2,2,2) stages 1..2;
+// LBM_TS_RK3_FUSED, stage 1 = the whole SSP-RK3 step (launch_fd_fused).
 cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int grid, const GroupDev& g, int j,
                             int stage, cudaStream_t s);
-// Stage launches per FD step of a scheme.
-inline int fd_stages(int scheme) { return scheme == LBM_TS_IMEX ? 2 : 3; }
+// Launches per FD step of a scheme.
+inline int fd_stages(int scheme) { return scheme == LBM_TS_IMEX ? 2 : (scheme == LBM_TS_RK3_FUSED ? 1 : 3); }
+// Temporally blocked SSP-RK3 step (kernels_fd_fused.cu): the three stages of
+// a step for every lattice of the group in one launch, buf[cur] -> buf[cur ^ 1]
+// (tile FD_T32x8 or FD_T32x4: output tiles of 32 x 8 or 32 x 4 nodes).
+cudaError_t launch_fd_fused(int precision, int q1, int tile, int grid, const GroupDev& g, int j, cudaStream_t s);
+bool fd_fused_fits(int precision, int q1, int tile);
+int fd_fused_blocks_per_sm(int precision, int q1, int tile);
 // Occupancy-based resident CTAs per SM of a variant (for persistent grids).
 int cs_blocks_per_sm(int precision, int tile);
-int fd_blocks_per_sm(int precision, int q1, int tile);
-// Whether an FD variant fits this device (shared memory); unfit variants are
-// refused by set_group_config and skipped by the autotuner.
-bool fd_variant_fits(int precision, int q1, int tile);
+int fd_blocks_per_sm(int precision, int q1, int tile, int scheme);
+// Whether an FD variant of a scheme fits this device (shared memory); unfit
+// variants are refused by set_group_config and skipped by the autotuner.
+bool fd_variant_fits(int precision, int q1, int tile, int scheme);
 
 // Fused-observables finalisation: lattices observing at sub-step j reduce
 // their tile partials (in nchunks chunks, scratch chunks[max_lat][nchunks][NOBS])

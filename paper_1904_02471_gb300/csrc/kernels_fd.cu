@@ -28,92 +28,11 @@
 // buf[2] = f^(2). Storage offset as in the CS kernel (deviation form for
 // FP32, full f for FP64): WENO differences and the stage combination are
 // unchanged by the constant offset w_k rho0.
+#include "fd_common.cuh"
 #include "kernels.h"
 #include "ptx.cuh"
 
 namespace lbm {
-
-// Pairs of values evaluated together: the x-face and the y-face of a node
-// are two independent WENO-5 reconstructions, computed side by side. For
-// float they map to the packed FP32x2 instructions of sm_100+ (one
-// instruction, two results); for double they are two scalar operations.
-template <typename T>
-struct Pr;
-
-template <>
-struct Pr<float> {
-    using V = float2;
-    static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
-    static __device__ __forceinline__ V sp(float a) { return make_float2(a, a); }
-    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
-    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
-    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
-    // a / b through the approximate reciprocal (relative error ~2^-23):
-    // b is a normal number far from the range limits here
-    static __device__ __forceinline__ float rcp(float x) {
-        float r;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-        return r;
-    }
-    static __device__ __forceinline__ V div(V a, V b) { return __fmul2_rn(a, make_float2(rcp(b.x), rcp(b.y))); }
-};
-
-template <>
-struct Pr<double> {
-    using V = double2;
-    static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
-    static __device__ __forceinline__ V sp(double a) { return make_double2(a, a); }
-    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
-    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
-    static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
-    static __device__ __forceinline__ V div(V a, V b) { return make_double2(a.x / b.x, a.y / b.y); }
-};
-
-// WENO-5 interface values (Jiang-Shu) of two faces at once, from their
-// upwind-ordered stencils (a, b, c, d, e) = (f_{i-2}, f_{i-1}, f_i, f_{i+1},
-// f_{i+2}) for the face i+1/2:
-//   candidates q0 = (2a - 7b + 11c)/6, q1 = (-b + 5c + 2d)/6, q2 = (2c + 5d - e)/6,
-//   smoothness beta_r = 13/12 t_r^2 + 1/4 u_r^2 with the second differences
-//     t_r and the first differences u0 = a - 4b + 3c, u1 = b - d,
-//     u2 = 3c - 4d + e of the three stencils,
-//   weights alpha_r = d_r / (eps + beta_r)^2, d = (1/10, 6/10, 3/10),
-//   face = sum alpha_r q_r / sum alpha_r.
-// The normalised weights do not change when every alpha_r is multiplied by
-// one common factor, so the kernel uses s_r = (12/13)(eps + beta_r) =
-// t_r^2 + (3/13) u_r^2 + e (e = 12 eps / 13, passed in), d = (1, 6, 3), and
-// multiplies numerator and denominator by s0^2 s1^2 s2^2: one reciprocal per
-// face. All differences come from the four node differences D_i = f_{i+1} - f_i
-// of the stencil (exact for close values). With q_r = c + (t_r + 3 u_r')/12
-// (u_r' = u0, -u1, -u2) the function returns 12 (face - c): a small number
-// next to c, so its rounding is small next to the flux differences it feeds.
-template <typename T>
-__device__ __forceinline__ typename Pr<T>::V weno5_pair(typename Pr<T>::V a, typename Pr<T>::V b, typename Pr<T>::V c,
-                                                        typename Pr<T>::V d, typename Pr<T>::V e, typename Pr<T>::V eps_s) {
-    using P = Pr<T>;
-    using V = typename P::V;
-    const V m1 = P::sp(T(-1));
-    const V D1 = P::fma(a, m1, b), D2 = P::fma(b, m1, c), D3 = P::fma(c, m1, d), D4 = P::fma(d, m1, e);
-    const V t0 = P::fma(D1, m1, D2), t1 = P::fma(D2, m1, D3), t2 = P::fma(D3, m1, D4);
-    const V u0 = P::fma(D2, P::sp(T(-3)), D1);   // -(a - 4b + 3c)
-    const V u1 = P::add(D2, D3);                  // d - b
-    const V u2 = P::fma(D3, P::sp(T(-3)), D4);   // 3c - 4d + e
-    const V q0 = P::fma(u0, P::sp(T(-3)), t0);   // 12 (q0 - c)
-    const V q1 = P::fma(u1, P::sp(T(3)), t1);    // 12 (q1 - c)
-    const V q2 = P::fma(u2, P::sp(T(-3)), t2);   // 12 (q2 - c)
-    const V k = P::sp(T(3.0 / 13.0));
-    V s0 = P::fma(t0, t0, P::fma(P::mul(u0, k), u0, eps_s));
-    V s1 = P::fma(t1, t1, P::fma(P::mul(u1, k), u1, eps_s));
-    V s2 = P::fma(t2, t2, P::fma(P::mul(u2, k), u2, eps_s));
-    s0 = P::mul(s0, s0);
-    s1 = P::mul(s1, s1);
-    s2 = P::mul(s2, s2);
-    const V w0 = P::mul(s1, s2);                          // d0 s1^2 s2^2
-    const V w1 = P::mul(P::mul(s0, s2), P::sp(T(6)));     // d1 s0^2 s2^2
-    const V w2 = P::mul(P::mul(s0, s1), P::sp(T(3)));     // d2 s0^2 s1^2
-    const V num = P::fma(q2, w2, P::fma(q1, w1, P::mul(q0, w0)));
-    const V den = P::add(P::add(w0, w1), w2);
-    return P::div(num, den);
-}
 
 // Column sums cs[ix] = sum_iy g(ix + Q1 iy) and row sums rs[iy] =
 // sum_ix g(ix + Q1 iy) of a quantity over the product set.
@@ -172,11 +91,6 @@ struct EqTerms {
         return GH<Q1>::v(ix) == 0.0 ? yl : xj(ix) + yl;
     }
 };
-
-__device__ __forceinline__ int wrapi(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
-}
 
 // Tile geometry: TX = 32 nodes along x (one warp per row), TY rows. The
 // staged halo tile of a population has HY = TY + 6 rows of HXP = 40 values,
@@ -817,8 +731,10 @@ static cudaError_t fd_prepare(int precision, int tile, int q1) {
 cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int grid, const GroupDev& g, int j,
                             int stage, cudaStream_t s) {
     if (tile < 0 || tile >= FD_NTILES || grid <= 0 || q1 < 3 || q1 > 5 ||
-        (scheme != LBM_TS_RK3 && scheme != LBM_TS_IMEX) || stage < 1 || stage > fd_stages(scheme))
+        (scheme != LBM_TS_RK3 && scheme != LBM_TS_IMEX && scheme != LBM_TS_RK3_FUSED) || stage < 1 ||
+        stage > fd_stages(scheme))
         return cudaErrorInvalidValue;
+    if (scheme == LBM_TS_RK3_FUSED) return launch_fd_fused(precision, q1, tile, grid, g, j, s);
     const void* fn = fd_fn(precision, tile, q1, scheme);
     cudaError_t e = fd_prepare(precision, tile, q1);
     if (e != cudaSuccess) return e;
@@ -828,12 +744,14 @@ cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int gri
     return cudaLaunchKernel(fn, dim3(grid), dim3(fd_tile_tx(tile), fd_tile_ty(tile)), args, fd_bytes(precision, tile, q1), s);
 }
 
-bool fd_variant_fits(int precision, int q1, int tile) {
+bool fd_variant_fits(int precision, int q1, int tile, int scheme) {
+    if (scheme == LBM_TS_RK3_FUSED) return fd_fused_fits(precision, q1, tile);
     return tile >= 0 && tile < FD_NTILES && q1 >= 3 && q1 <= 5 && fd_prepare(precision, tile, q1) == cudaSuccess;
 }
 
-int fd_blocks_per_sm(int precision, int q1, int tile) {
-    if (!fd_variant_fits(precision, q1, tile)) return 1;
+int fd_blocks_per_sm(int precision, int q1, int tile, int scheme) {
+    if (scheme == LBM_TS_RK3_FUSED) return fd_fused_blocks_per_sm(precision, q1, tile);
+    if (!fd_variant_fits(precision, q1, tile, scheme)) return 1;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fd_fn(precision, tile, q1, LBM_TS_RK3),
                                                       fd_tile_tx(tile) * fd_tile_ty(tile),

@@ -16,11 +16,12 @@
 
 namespace lbm {
 
-// Buffer that holds a lattice's current state (two-buffer CS: the current
-// one of the pair; in-place CS and FD: buffer 0).
+// Buffer that holds a lattice's current state: the current one of the pair
+// (two-buffer CS, temporally blocked FD); buffer 0 for in-place CS, and for
+// RK3 / IMEX FD, whose cur stays 0.
 template <bool PULL>
 __device__ __forceinline__ int store_buf(const LatDesc* d) {
-    return PULL && !d->inplace ? d->cur : 0;
+    return PULL && d->inplace ? 0 : d->cur;
 }
 
 template <typename T, int Q1, bool PULL>

@@ -255,8 +255,8 @@ MODELS = {"cs": LBM_CS, "fd": LBM_FD}
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp32dev": LBM_FP32_DEV}
 LBM_STORE_AB, LBM_STORE_INPLACE = 0, 1
 STORAGES = {"ab": LBM_STORE_AB, "inplace": LBM_STORE_INPLACE}
-LBM_TS_RK3, LBM_TS_IMEX = 0, 1
-SCHEMES = {"rk3": LBM_TS_RK3, "imex": LBM_TS_IMEX}
+LBM_TS_RK3, LBM_TS_IMEX, LBM_TS_RK3_FUSED = 0, 1, 2
+SCHEMES = {"rk3": LBM_TS_RK3, "imex": LBM_TS_IMEX, "rk3_fused": LBM_TS_RK3_FUSED}
 
 
 def make_spec(model, q, nx, ny, tau, dt=0.0, dx=0.0, precision="fp64", rho0=0.0, storage="ab",

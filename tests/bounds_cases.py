@@ -1,5 +1,6 @@
 """Cases run against the bounds-checked build of the library (the library
-selected by LBM_LIBRARY): every CS and FD kernel variant, both CS storages,
+selected by LBM_LIBRARY): every CS and FD kernel variant (FD: also the
+temporally blocked step), both CS storages,
 both precisions, ragged and degenerate sizes, batches with step budgets,
 region readouts that wrap, checkpoints. A kernel that reaches outside a state
 buffer makes the step fail with LBM_ECUDA; FP64 results are also checked
@@ -77,6 +78,38 @@ def fd_cases():
     return n
 
 
+def fused_cases():
+    """Temporally blocked FD steps: halos of 9 nodes that wrap (also several
+    times around lattices smaller than the halo), interior tiles staged
+    without wrap, an odd step count (the state ends in the second buffer)."""
+    n = 0
+    for q in (3, 4, 5):
+        for nx, ny in [(1, 1), (6, 6), (7, 9), (40, 17), (70, 33), (96, 40)]:
+            rho, ux, uy = wl.random_smooth(nx, ny, seed=q + 3 * nx + ny, amp_rho=0.05, amp_u=0.05)
+            f0 = oracle.equilibrium(q, rho, ux, uy)
+            dt = 0.4 * pkg.lbm_fd_max_dt(q, 1.0 / nx, 1e300)
+            tau = 2 * dt
+            ref = oracle.fd_run(f0, 1.0 / nx, dt, tau, 3)
+            for prec in ("fp64", "fp32"):
+                for tile in range(lbm.lbm_n_tiles("fd")):
+                    with pkg.Lattice("fd", q, nx, ny, tau, dt=dt, precision=prec, scheme="rk3_fused") as L:
+                        try:
+                            L.config(tile, 3)
+                        except lbm.LbmError as e:  # no fused kernel for this tile, or too large
+                            assert e.code == lbm.LBM_EINVAL
+                            continue
+                        L.set_populations(f0)
+                        L.step(3)
+                        L.sync()
+                        f = L.populations()
+                        L.observables()
+                        L.populations_region(max(nx - 2, 0), 0, min(5, nx), min(3, ny))
+                        if prec == "fp64":
+                            assert rel_err(f, ref) < 1e-12, (q, nx, ny, tile)
+                        n += 1
+    return n
+
+
 def batch_case():
     cfg = [("cs", 3, 130, 17, 0.42, 0.0, "fp64", "inplace"), ("fd", 4, 40, 33, 2e-3, 1e-3, "fp32", "ab"),
            ("cs", 3, 7, 300, 0.31, 0.0, "fp32", "ab"), ("fd", 5, 24, 24, 3e-3, 1e-3, "fp64", "ab"),
@@ -115,9 +148,10 @@ def main():
     torch.cuda.init()
     n_cs = cs_cases()
     n_fd = fd_cases()
+    n_ff = fused_cases()
     batch_case()
     checkpoint_case()
-    print(f"bounds-checked runs ok: {n_cs} CS, {n_fd} FD, batch, checkpoint")
+    print(f"bounds-checked runs ok: {n_cs} CS, {n_fd} FD, {n_ff} fused FD, batch, checkpoint")
 
 
 if __name__ == "__main__":

@@ -130,7 +130,8 @@ def test_kernel_digest_follows_code_not_comments():
     """The digest that ties a recorded DRAM-traffic figure to a kernel's
     sources ignores comments and layout, and changes with the code."""
     from paper_1904_02471_gb300 import build
-    base = {"kernels_fd.cu": "int f(int a) { return a + 1; } // one\n", "common.cuh": "/* c */ #define X 1\n",
+    base = {"kernels_fd.cu": "int f(int a) { return a + 1; } // one\n", "fd_common.cuh": "int g();\n",
+            "common.cuh": "/* c */ #define X 1\n",
             "ptx.cuh": 'const char* s = "a // not a comment";\n', "kernels.h": ""}
     d0 = build.kernel_digest("fd_stage", base.__getitem__)
     relaid = dict(base, **{"kernels_fd.cu": "// header\nint f(int a)\n{\n    return a + 1;  /* two */\n}\n"})
@@ -242,6 +243,9 @@ def test_spec_from_nu_validation(args, code):
     (dict(model="cs", q=3, tau=0.5, dt=0.0, scheme="imex"), lbm.LBM_EINVAL),    # the scheme is an FD choice
     (dict(model="fd", q=4, tau=1e-4, dt=1e-3, scheme=7), lbm.LBM_EINVAL),
     (dict(model="fd", q=4, tau=1e-4, dt=2e-2, scheme="imex"), lbm.LBM_ECFL),    # IMEX keeps the CFL bound
+    (dict(model="fd", q=4, tau=1e-4, dt=1e-3, scheme="rk3_fused"), lbm.LBM_ESTIFF),  # the fused RK3 step too
+    (dict(model="cs", q=3, tau=0.5, dt=0.0, scheme="rk3_fused"), lbm.LBM_EINVAL),
+    (dict(model="fd", q=4, tau=1e-2, dt=2e-2, scheme="rk3_fused"), lbm.LBM_ECFL),
 ])
 def test_scheme_validation(kw, code):
     """IMEX lifts dt <= tau (Sec. 4.1) and nothing else; the RK3 default
