@@ -716,6 +716,7 @@ def run_fused(torch, n=FD_N, steps=20, warm=3):
         spec = pkg.make_spec("fd", 4, n, n, FD_TAU, FD_DT, 0.0, "fp32", scheme=scheme)
         B = pkg.Batch([spec])
         B.init(0, *wl.taylor_green(n, n, U0))
+        tuning = B.tune(2)
         B.record(0, steps, 4)
         B.step_profiled(warm)
         ms, total = B.step_profiled(steps)
@@ -729,7 +730,7 @@ def run_fused(torch, n=FD_N, steps=20, warm=3):
                        "ms_per_step": round(step_ms, 4), "mlups": round(n * n / (step_ms / 1e3) / 1e6, 1),
                        "gbs": round(n * n * bytes_lu / (step_ms / 1e3) / 1e9, 1), "bytes_per_lu": bytes_lu,
                        "frac_hbm": round(n * n * bytes_lu / (step_ms / 1e3) / 1e9 / peaks()[0], 4),
-                       "finite": all(x["nonfinite"] == 0 for x in ser)}
+                       "tuning": tuning.strip(), "finite": all(x["nonfinite"] == 0 for x in ser)}
     out["fused_over_rk3"] = round(out["rk3_fused"]["mlups"] / out["rk3"]["mlups"], 3)
     return out
 

@@ -38,7 +38,8 @@ cudaError_t launch_fd_stage(int precision, int q1, int scheme, int tile, int gri
 inline int fd_stages(int scheme) { return scheme == LBM_TS_IMEX ? 2 : (scheme == LBM_TS_RK3_FUSED ? 1 : 3); }
 // Temporally blocked SSP-RK3 step (kernels_fd_fused.cu): the three stages of
 // a step for every lattice of the group in one launch, buf[cur] -> buf[cur ^ 1]
-// (tile FD_T32x8 or FD_T32x4: output tiles of 32 x 8 or 32 x 4 nodes).
+// (tile FD_T32x16, FD_T32x8 or FD_T32x4: output tiles of 32 x 16, 32 x 8 or
+// 32 x 4 nodes, where they fit the device's shared memory).
 cudaError_t launch_fd_fused(int precision, int q1, int tile, int grid, const GroupDev& g, int j, cudaStream_t s);
 bool fd_fused_fits(int precision, int q1, int tile);
 int fd_fused_blocks_per_sm(int precision, int q1, int tile);

@@ -35,10 +35,18 @@
 
 namespace lbm {
 
+// cp.async groups: close the group of copies issued so far; wait until at
+// most N groups are still in flight
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_prior() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <typename T, int Q1, int TY>
 struct FusedGeo {
     static constexpr int K = Q1 * Q1;
-    static constexpr int NT = sizeof(T) == 4 ? 512 : 256;   // threads per block
+    static constexpr int NT = sizeof(T) == 4 ? 1024 : 256;  // threads per block
     static constexpr int G = sizeof(T) == 4 ? 4 : 2;        // populations per face group
     static constexpr int VEC = 16 / (int)sizeof(T);         // values per 16-byte copy
     // staged f^n of a group: columns x0 - 12 .. x0 + 43 (16-byte aligned
@@ -58,11 +66,17 @@ struct FusedGeo {
     static constexpr size_t n_r0 = (size_t)G * H0 * W0;
     static constexpr size_t n_f = (size_t)G * FH * FW;
     static constexpr size_t n_m = (size_t)NM * H1 * W1;
-    static constexpr size_t bytes = sizeof(T) * (n_s1 + n_r0 + 2 * n_f + n_m) + sizeof(double) * (NT / 32) * NOBS;
-    // stage 2 results held per thread before the in-place write
-    static constexpr int NR2 = (G * H2 * W2 + NT - 1) / NT;
+    static constexpr size_t n_red = sizeof(double) * (NT / 32) * NOBS;
+    // two staging buffers (the next group's f^n is copied while the current
+    // group computes) where they fit next to the rest (opt-in limit of the
+    // device, 227 KiB, less 2 KiB for the static shared variables), else one
+    static constexpr int NB = sizeof(T) * (n_s1 + 2 * n_r0 + 2 * n_f + n_m) + n_red <= 227 * 1024 - 2048 ? 2 : 1;
+    static constexpr size_t bytes = sizeof(T) * (n_s1 + NB * n_r0 + 2 * n_f + n_m) + n_red;
+    // stage 2 nodes per thread (results held before the in-place write)
+    static constexpr int NR2 = (H2 * W2 + NT - 1) / NT;
     static_assert((n_s1 * sizeof(T)) % 16 == 0 && (W0 * sizeof(T)) % 16 == 0, "16-byte aligned staging rows");
-    static_assert(((n_s1 + n_r0 + 2 * n_f + n_m) * sizeof(T)) % 8 == 0, "aligned reduction scratch");
+    static_assert(((n_s1 + n_r0 + 2 * n_f + n_m) * sizeof(T)) % 8 == 0 && (n_r0 * sizeof(T)) % 16 == 0,
+                  "aligned staging buffers and reduction scratch");
 };
 
 // x- and y-face on the low side of the node at (R, C) of a region stored
@@ -90,8 +104,8 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
     constexpr int N1 = H1 * W1;   // nodes of R1 (plane of the f^(1) buffer)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s1 = reinterpret_cast<T*>(smem_raw);   // [K][H1][W1]: f^(1) on R1, then f^(2) on R2
-    T* r0 = s1 + Ge::n_s1;                     // [G][H0][W0]: f^n of the group's populations
-    T* fxs = r0 + Ge::n_r0;                    // [G][FH][FW]
+    T* r0 = s1 + Ge::n_s1;                     // [NB][G][H0][W0]: f^n of a group's populations
+    T* fxs = r0 + Ge::NB * Ge::n_r0;           // [G][FH][FW]
     T* fys = fxs + Ge::n_f;                    // [G][FH][FW]
     T* mom = fys + Ge::n_f;                    // [NM][N1]
     double* red = reinterpret_cast<double*>(mom + Ge::n_m);
@@ -177,48 +191,109 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
             mom[4 * N1 + p] = jx + R1x;
             mom[5 * N1 + p] = jy + R1y;
         };
-        // dt L(u)_k of one node and population from its four faces, its
-        // upwind neighbours and the stored moments (stage kernels' formulas)
-        auto increment = [&](int k, int p, T uk, T fxl, T fxh, T fyl, T fyh, T dcx, T dcy) {
-            const T vx = s_vx[k], vy = s_vy[k];
-            T a = T(0);
-            if (vx != T(0)) a = vx * ((fxh - fxl) * T(1.0 / 12.0) + dcx);
-            if (vy != T(0)) a += vy * ((fyh - fyl) * T(1.0 / 12.0) + dcy);
-            const T ux = mom[0 * N1 + p], uy = mom[1 * N1 + p], hr = mom[2 * N1 + p];
-            const T drc = mom[3 * N1 + p], jxc = mom[4 * N1 + p], jyc = mom[5 * N1 + p];
-            const T usq = ux * ux + uy * uy;
-            const T xi = vx * ux + vy * uy;
-            const T geq = s_w[k] * (hr * (xi * xi - usq) + (vx * jxc + (vy * jyc + drc)));
-            return (geq - uk) * dtt - a * cdx;
+        // the stored moments of a node (formed once per node and stage)
+        struct NodeM {
+            T ux, uy, usq, hr, drc, jxc, jyc;
+        };
+        auto load_m = [&](int p) {
+            NodeM m;
+            m.ux = mom[0 * N1 + p];
+            m.uy = mom[1 * N1 + p];
+            m.hr = mom[2 * N1 + p];
+            m.drc = mom[3 * N1 + p];
+            m.jxc = mom[4 * N1 + p];
+            m.jyc = mom[5 * N1 + p];
+            m.usq = m.ux * m.ux + m.uy * m.uy;
+            return m;
+        };
+        // velocity components and weights of a group's populations (uniform
+        // across the block), loaded once per group
+        struct GroupC {
+            T vx[G], vy[G], w[G];
+        };
+        auto group_consts = [&](int k0) {
+            GroupC gc;
+#pragma unroll
+            for (int pp = 0; pp < G; ++pp) {
+                const int k = k0 + pp < K ? k0 + pp : K - 1;
+                gc.vx[pp] = s_vx[k];
+                gc.vy[pp] = s_vy[k];
+                gc.w[pp] = s_w[k];
+            }
+            return gc;
         };
         // faces of the group's populations on a region of W x H nodes whose
         // node (r, c) sits at (r + OY, c + OX) of the input `in` (row width
-        // WI, population planes `pl` apart)
-        auto group_faces = [&](const T* in, long long pl, int WI, int OY, int OX, int W, int H, int k0, int ng) {
+        // WI, population planes `pl` apart): positions outer, populations inner
+        auto group_faces = [&](const GroupC& gc, const T* in, long long pl, int WI, int OY, int OX, int W, int H,
+                               int ng) {
             const int npos = (H + 1) * (W + 1);
-            for (int t = tid; t < ng * npos; t += NT) {
-                const int pp = t / npos, pos = t - pp * npos;
+            for (int pos = tid; pos < npos; pos += NT) {
                 const int r = pos / (W + 1), c = pos - r * (W + 1);
-                const int k = k0 + pp;
-                const V f = fused_faces<T>(in + pp * pl, WI, r + OY, c + OX, s_vx[k] > T(0), s_vy[k] > T(0), eps);
-                if (r < H) fxs[pp * Ge::FH * FW + r * FW + c] = f.x;
-                if (c < W) fys[pp * Ge::FH * FW + r * FW + c] = f.y;
+#pragma unroll
+                for (int pp = 0; pp < G; ++pp) {
+                    if (pp < ng) {
+                        const V f = fused_faces<T>(in + pp * pl, WI, r + OY, c + OX, gc.vx[pp] > T(0), gc.vy[pp] > T(0),
+                                                   eps);
+                        if (r < H) fxs[pp * Ge::FH * FW + r * FW + c] = f.x;
+                        if (c < W) fys[pp * Ge::FH * FW + r * FW + c] = f.y;
+                    }
+                }
             }
         };
-        // dt L of node (r, c) of a region (input as in group_faces)
-        auto node_inc = [&](const T* tk, int WI, int OY, int OX, int W, int pp, int k, int r, int c, T& uk) {
+        // dt L(u)_k of population pp of the group at node (r, c) of a region
+        // (input as in group_faces) from its four faces, its upwind
+        // neighbours and the node's moments (the stage kernels' formulas);
+        // uk = the stage input at the node
+        auto node_inc = [&](const GroupC& gc, const NodeM& m, const T* tk, int WI, int OY, int OX, int pp, int r, int c,
+                            T& uk) {
             const int R = r + OY, C = c + OX;
             uk = tk[R * WI + C];
-            const T vx = s_vx[k], vy = s_vy[k];
+            const T vx = gc.vx[pp], vy = gc.vy[pp];
             const T dcx = vx > T(0) ? uk - tk[R * WI + C - 1] : tk[R * WI + C + 1] - uk;
             const T dcy = vy > T(0) ? uk - tk[(R - 1) * WI + C] : tk[(R + 1) * WI + C] - uk;
             const T* fx = fxs + pp * Ge::FH * FW;
             const T* fy = fys + pp * Ge::FH * FW;
-            return increment(k, r * W + c, uk, fx[r * FW + c], fx[r * FW + c + 1], fy[r * FW + c], fy[(r + 1) * FW + c],
-                             dcx, dcy);
+            T a = T(0);
+            if (vx != T(0)) a = vx * ((fx[r * FW + c + 1] - fx[r * FW + c]) * T(1.0 / 12.0) + dcx);
+            if (vy != T(0)) a += vy * ((fy[(r + 1) * FW + c] - fy[r * FW + c]) * T(1.0 / 12.0) + dcy);
+            const T xi = vx * m.ux + vy * m.uy;
+            const T geq = gc.w[pp] * (m.hr * (xi * xi - m.usq) + (vx * m.jxc + (vy * m.jyc + m.drc)));
+            return (geq - uk) * dtt - a * cdx;
+        };
+
+        // asynchronous copies of the halo tiles of f^n (rows y0 - 9 .., columns
+        // x0 - 12 ..) of populations k0 .. k0 + G - 1 into dst
+        auto stage_group = [&](int k0, T* dst) {
+            const int ng = K - k0 < G ? K - k0 : G;
+            constexpr int RV = W0 / VEC;   // 16-byte chunks per staged row
+            if (interior || nx % VEC == 0) {
+                // interior: rows are 16-byte aligned (x0 - 12 is a multiple of
+                // VEC, the pitch of 32); periodic edge with nx a multiple of
+                // VEC: no chunk straddles the wrap point
+                for (int t = tid; t < ng * H0 * RV; t += NT) {
+                    const int pp = t / (H0 * RV), rem = t - pp * (H0 * RV);
+                    const int r = rem / RV, cc = rem - r * RV;
+                    const long long src = (long long)(k0 + pp) * plane +
+                                          (interior ? (long long)(y0 - 9 + r) * pitch + (x0 - 12 + cc * VEC)
+                                                    : s_row[r] + s_col[cc * VEC]);
+                    if (LBM_BC_NODE(dp, K, src) && LBM_BC_NODE(dp, K, src + VEC - 1))
+                        cp_async16(dst + pp * H0 * W0 + r * W0 + cc * VEC, Fn + src);
+                }
+            } else {
+                for (int t = tid; t < ng * H0 * W0; t += NT) {
+                    const int pp = t / (H0 * W0), rem = t - pp * (H0 * W0);
+                    const int r = rem / W0, c = rem - r * W0;
+                    const long long src = (long long)(k0 + pp) * plane + s_row[r] + s_col[c];
+                    if (LBM_BC_NODE(dp, K, src)) cp_async_small<sizeof(T)>(dst + rem + pp * H0 * W0, Fn + src);
+                }
+            }
         };
 
         // ---- stage 1: f^(1) = f^n + dt L(f^n) on R1 ----
+        // the first group's f^n tiles are copied while the moments are formed
+        stage_group(0, r0);
+        cp_async_commit();
         // moments of f^n at the R1 nodes (read from device memory), and the
         // observables of f^n over the tile's own nodes
         {
@@ -254,43 +329,39 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
             // no trailing barrier: `red` is next written after this item's barriers
             if (s_obs) block_reduce_obs<T, NT, false>(acc, dp->partials + (long long)local * NOBS, red);
         }
-        for (int k0 = 0; k0 < K; k0 += G) {
+        for (int k0 = 0, gi = 0; k0 < K; k0 += G, ++gi) {
             const int ng = K - k0 < G ? K - k0 : G;
-            // the group's halo tiles of f^n
-            constexpr int RV = W0 / VEC;   // 16-byte chunks per staged row
-            if (interior || nx % VEC == 0) {
-                // interior: rows are 16-byte aligned (x0 - 12 is a multiple of
-                // VEC, the pitch of 32); periodic edge with nx a multiple of
-                // VEC: no chunk straddles the wrap point
-                for (int t = tid; t < ng * H0 * RV; t += NT) {
-                    const int pp = t / (H0 * RV), rem = t - pp * (H0 * RV);
-                    const int r = rem / RV, cc = rem - r * RV;
-                    const long long src = (long long)(k0 + pp) * plane +
-                                          (interior ? (long long)(y0 - 9 + r) * pitch + (x0 - 12 + cc * VEC)
-                                                    : s_row[r] + s_col[cc * VEC]);
-                    if (LBM_BC_NODE(dp, K, src) && LBM_BC_NODE(dp, K, src + VEC - 1))
-                        cp_async16(r0 + pp * H0 * W0 + r * W0 + cc * VEC, Fn + src);
-                }
+            T* rg = r0 + (gi % Ge::NB) * Ge::n_r0;   // this group's staged f^n
+            if (Ge::NB == 2 && k0 + G < K) {
+                // copy the next group's tiles into the other buffer (free since
+                // the previous group's last barrier), wait for this group's
+                stage_group(k0 + G, r0 + ((gi + 1) % 2) * Ge::n_r0);
+                cp_async_commit();
+                cp_async_wait_prior<1>();
             } else {
-                for (int t = tid; t < ng * H0 * W0; t += NT) {
-                    const int pp = t / (H0 * W0), rem = t - pp * (H0 * W0);
-                    const int r = rem / W0, c = rem - r * W0;
-                    const long long src = (long long)(k0 + pp) * plane + s_row[r] + s_col[c];
-                    if (LBM_BC_NODE(dp, K, src)) cp_async_small<sizeof(T)>(r0 + rem + pp * H0 * W0, Fn + src);
-                }
+                cp_async_wait_prior<0>();
             }
-            cp_async_wait_all();
             __syncthreads();
-            group_faces(r0, (long long)H0 * W0, W0, 3, 6, W1, H1, k0, ng);
+            const GroupC gc = group_consts(k0);
+            group_faces(gc, rg, (long long)H0 * W0, W0, 3, 6, W1, H1, ng);
             __syncthreads();
-            for (int t = tid; t < ng * N1; t += NT) {
-                const int pp = t / N1, p = t - pp * N1;
+            for (int p = tid; p < N1; p += NT) {
                 const int r = p / W1, c = p - r * W1;
-                T uk;
-                const T inc = node_inc(r0 + pp * H0 * W0, W0, 3, 6, W1, pp, k0 + pp, r, c, uk);
-                s1[(k0 + pp) * N1 + p] = uk + inc;
+                const NodeM m = load_m(p);
+#pragma unroll
+                for (int pp = 0; pp < G; ++pp) {
+                    if (pp < ng) {
+                        T uk;
+                        const T inc = node_inc(gc, m, rg + pp * H0 * W0, W0, 3, 6, pp, r, c, uk);
+                        s1[(k0 + pp) * N1 + p] = uk + inc;
+                    }
+                }
             }
             __syncthreads();   // before the next group's staging and faces
+            if (Ge::NB == 1 && k0 + G < K) {
+                stage_group(k0 + G, r0);
+                cp_async_commit();
+            }
         }
 
         // ---- stage 2: f^(2) = f^n + 1/4 ((f^(1) - f^n) + dt L(f^(1))) on R2 ----
@@ -305,31 +376,38 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
         __syncthreads();
         for (int k0 = 0; k0 < K; k0 += G) {
             const int ng = K - k0 < G ? K - k0 : G;
-            group_faces(s1 + k0 * N1, (long long)N1, W1, 3, 3, W2, H2, k0, ng);
+            const GroupC gc = group_consts(k0);
+            group_faces(gc, s1 + k0 * N1, (long long)N1, W1, 3, 3, W2, H2, ng);
             __syncthreads();
-            T res[Ge::NR2];
+            T res[Ge::NR2][G];
 #pragma unroll
             for (int i = 0; i < Ge::NR2; ++i) {
-                const int t = tid + i * NT;
-                if (t < ng * H2 * W2) {
-                    const int pp = t / (H2 * W2), p = t - pp * (H2 * W2);
+                const int p = tid + i * NT;
+                if (p < H2 * W2) {
                     const int r = p / W2, c = p - r * W2;
-                    const int k = k0 + pp;
-                    T uk;
-                    const T inc = node_inc(s1 + k * N1, W1, 3, 3, W2, pp, k, r, c, uk);
-                    const long long off = (long long)k * plane + s_row[r + 6] + s_col[c + 9];
-                    const T fn = LBM_BC_NODE(dp, K, off) ? Fn[off] : T(0);
-                    res[i] = fn + T(0.25) * ((uk - fn) + inc);
+                    const NodeM m = load_m(p);
+#pragma unroll
+                    for (int pp = 0; pp < G; ++pp) {
+                        if (pp < ng) {
+                            const int k = k0 + pp;
+                            T uk;
+                            const T inc = node_inc(gc, m, s1 + k * N1, W1, 3, 3, pp, r, c, uk);
+                            const long long off = (long long)k * plane + s_row[r + 6] + s_col[c + 9];
+                            const T fn = LBM_BC_NODE(dp, K, off) ? Fn[off] : T(0);
+                            res[i][pp] = fn + T(0.25) * ((uk - fn) + inc);
+                        }
+                    }
                 }
             }
             __syncthreads();   // every old value of the group has been read
 #pragma unroll
             for (int i = 0; i < Ge::NR2; ++i) {
-                const int t = tid + i * NT;
-                if (t < ng * H2 * W2) {
-                    const int pp = t / (H2 * W2), p = t - pp * (H2 * W2);
+                const int p = tid + i * NT;
+                if (p < H2 * W2) {
                     const int r = p / W2, c = p - r * W2;
-                    s1[(k0 + pp) * N1 + (r + 3) * W1 + c + 3] = res[i];
+#pragma unroll
+                    for (int pp = 0; pp < G; ++pp)
+                        if (pp < ng) s1[(k0 + pp) * N1 + (r + 3) * W1 + c + 3] = res[i][pp];
                 }
             }
         }
@@ -347,20 +425,26 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
         __syncthreads();
         for (int k0 = 0; k0 < K; k0 += G) {
             const int ng = K - k0 < G ? K - k0 : G;
-            group_faces(s1 + k0 * N1, (long long)N1, W1, 6, 6, 32, TY, k0, ng);
+            const GroupC gc = group_consts(k0);
+            group_faces(gc, s1 + k0 * N1, (long long)N1, W1, 6, 6, 32, TY, ng);
             __syncthreads();
-            for (int t = tid; t < ng * TY * 32; t += NT) {
-                const int pp = t / (TY * 32), p = t - pp * (TY * 32);
+            for (int p = tid; p < TY * 32; p += NT) {
                 const int r = p / 32, c = p - r * 32;
                 const int x = x0 + c, y = y0 + r;
                 if (x < nx && y < ny) {
-                    const int k = k0 + pp;
-                    T uk;
-                    const T inc = node_inc(s1 + k * N1, W1, 6, 6, 32, pp, k, r, c, uk);
-                    const long long off = (long long)k * plane + (long long)y * pitch + x;
-                    if (LBM_BC_NODE(dp, K, off)) {
-                        const T fn = Fn[off];
-                        out[off] = fn + T(2.0 / 3.0) * ((uk - fn) + inc);
+                    const NodeM m = load_m(p);
+#pragma unroll
+                    for (int pp = 0; pp < G; ++pp) {
+                        if (pp < ng) {
+                            const int k = k0 + pp;
+                            T uk;
+                            const T inc = node_inc(gc, m, s1 + k * N1, W1, 6, 6, pp, r, c, uk);
+                            const long long off = (long long)k * plane + (long long)y * pitch + x;
+                            if (LBM_BC_NODE(dp, K, off)) {
+                                const T fn = Fn[off];
+                                out[off] = fn + T(2.0 / 3.0) * ((uk - fn) + inc);
+                            }
+                        }
                     }
                 }
             }
@@ -369,12 +453,19 @@ __global__ void __launch_bounds__(FusedGeo<T, Q1, TY>::NT, 1) fd_fused_kernel(Gr
     }
 }
 
-// Output tile heights of the fused kernel: 8 or 4 rows (FD_T32x8, FD_T32x4).
-static int fused_ty(int tile) { return tile == FD_T32x8 ? 8 : (tile == FD_T32x4 ? 4 : 0); }
+// Output tile heights of the fused kernel: 16, 8 or 4 rows (FD_T32x16,
+// FD_T32x8, FD_T32x4). Taller tiles spend fewer node-stages on the halo
+// (per output node: 5.0 for 32 x 16, 6.5 for 32 x 8, 9.6 for 32 x 4) but
+// need more shared memory.
+static int fused_ty(int tile) {
+    return tile == FD_T32x16 ? 16 : (tile == FD_T32x8 ? 8 : (tile == FD_T32x4 ? 4 : 0));
+}
 
 template <typename T, int Q1>
 static const void* fused_ptr_q(int ty) {
-    return ty == 8 ? (const void*)fd_fused_kernel<T, Q1, 8> : (ty == 4 ? (const void*)fd_fused_kernel<T, Q1, 4> : nullptr);
+    return ty == 16 ? (const void*)fd_fused_kernel<T, Q1, 16>
+                    : (ty == 8 ? (const void*)fd_fused_kernel<T, Q1, 8>
+                               : (ty == 4 ? (const void*)fd_fused_kernel<T, Q1, 4> : nullptr));
 }
 template <typename T>
 static const void* fused_ptr(int q1, int ty) {
@@ -382,14 +473,15 @@ static const void* fused_ptr(int q1, int ty) {
 }
 template <typename T, int Q1>
 static size_t fused_bytes_q(int ty) {
-    return ty == 8 ? FusedGeo<T, Q1, 8>::bytes : (ty == 4 ? FusedGeo<T, Q1, 4>::bytes : 0);
+    return ty == 16 ? FusedGeo<T, Q1, 16>::bytes
+                    : (ty == 8 ? FusedGeo<T, Q1, 8>::bytes : (ty == 4 ? FusedGeo<T, Q1, 4>::bytes : 0));
 }
 template <typename T>
 static size_t fused_bytes_t(int q1, int ty) {
     return q1 == 3 ? fused_bytes_q<T, 3>(ty) : (q1 == 4 ? fused_bytes_q<T, 4>(ty) : (q1 == 5 ? fused_bytes_q<T, 5>(ty) : 0));
 }
 
-int fd_fused_threads(int precision) { return precision == LBM_FP64 ? 256 : 512; }
+int fd_fused_threads(int precision) { return precision == LBM_FP64 ? 256 : 1024; }
 
 // Opt a variant into the dynamic shared memory it needs; once per process.
 // Variants that do not fit the device (or tile shapes without a fused
