@@ -82,13 +82,16 @@ void initial_fields(const lbm_request& q, std::vector<double>& rho, std::vector<
 // between runs: about 20 us of fixed cost per step (launch and tile latency
 // of a small lattice) plus a cost per node, from single-lattice rates on
 // GB300 (FP32: CS D2Q9 in place 74 GLUPS, FD 16-velocity 4.4 GLUPS, the FD
-// cost scaled by the number of velocities; FP64 on the narrow FP64 pipe).
-// Only the ratios between runs matter.
+// cost scaled by the number of velocities; FP64 on the narrow FP64 pipe; an
+// FD step with the IMEX scheme 1.1x, temporally blocked 3.0x the RK3 step,
+// as measured for FD 16-velocity 4096^2). Only the ratios between runs matter.
 double step_cost(const lbm_spec& s) {
     const double nodes = (double)s.nx * s.ny;
     const double k = (double)s.q_per_axis * s.q_per_axis;
+    const double scheme = s.model == LBM_CS ? 1.0
+                          : (s.scheme == LBM_TS_IMEX ? 1.1 : (s.scheme == LBM_TS_RK3_FUSED ? 3.0 : 1.0));
     const double per_node = s.model == LBM_CS ? (s.precision == LBM_FP64 ? 0.125e-9 : 0.0135e-9)
-                                              : (s.precision == LBM_FP64 ? 6e-9 : 0.227e-9) * k / 16.0;
+                                              : (s.precision == LBM_FP64 ? 6e-9 : 0.227e-9) * k / 16.0 * scheme;
     return 20e-6 + nodes * per_node;
 }
 

@@ -182,6 +182,10 @@ def test_server_round_plan():
     assert lbm.plan_round([cs(256), cs(256)], [500, 500], 16) == [16, 16]       # equal costs, equal steps
     a, b = lbm.plan_round([cs(2048), cs(2048, "fp64")], [10 ** 6, 10 ** 6], 64)
     assert a == 64 and 1 <= b < a                                               # FP64 costs more
+    fused = fd(512)
+    fused.scheme = lbm.LBM_TS_RK3_FUSED
+    a, b = lbm.plan_round([fd(512), fused], [10 ** 6, 10 ** 6], 64)
+    assert a == 64 and 1 <= b < a                                               # the blocked step costs more
     assert lbm.plan_round([], [], 8) == []
     for args in (([cs(64)], [1], 0), ([cs(64)], [-1], 8)):
         with pytest.raises(lbm.LbmError) as e:
