@@ -34,12 +34,12 @@ def _cs(n, tau, prec="fp32"):
     return pkg.make_spec("cs", 3, n, n, tau, 0.0, 0.0, prec)
 
 
-def _fd(n, q, prec="fp32", tau_star=0.9):
+def _fd(n, q, prec="fp32", tau_star=0.9, scheme="rk3"):
     # dt <= tau and a Courant number of 0.4 (CFL = 1 is unstable for
     # WENO-5 + RK3 advection along both axes)
     tau = pkg.lbm_tau_fd_from_lu(n, tau_star / SQ3)
     dt = min(tau, 0.4 * pkg.lbm_fd_max_dt(q, 1.0 / n, 1e300))
-    return pkg.make_spec("fd", q, n, n, tau, dt, 0.0, prec)
+    return pkg.make_spec("fd", q, n, n, tau, dt, 0.0, prec, scheme=scheme)
 
 
 MIX = [
@@ -51,6 +51,8 @@ MIX = [
     (lambda: _fd(40, 4), 260, "shock", 0.0),
     (lambda: _cs(128, 0.35), 100, "shock", 0.0),
     (lambda: _fd(56, 4, "fp32", 1.4), 330, "tg", 0.01),
+    (lambda: _fd(44, 4, "fp32", 1.1, "rk3_fused"), 170, "tg", 0.01),   # temporally blocked step
+    (lambda: _fd(36, 3, "fp64", 0.8, "rk3_fused"), 90, "shear", 0.01),
 ]
 
 
