@@ -17,7 +17,8 @@ observables out); the batched leg (256 mixed lattices in FP32 against each
 lattice alone in FP64 for the same steps, with the FP32 velocity and
 decay-rate errors); the served leg (a Poisson stream of CS / FD runs of
 64^2..4096^2 nodes and 1k..20k steps into the continuous-batching server:
-p50/p99 latency and slowdown, aggregate rate, FP32 errors of every run up to
+p50/p99 latency and slowdown, aggregate rate against the plain FP64 form of
+the same request list run one at a time, FP32 errors of every run up to
 256^2 against FP64); the IMEX leg (FD 16-velocity 4096^2 with tau below the
 Courant-limited step: RK3 at dt = tau against IMEX at the Courant limit); the
 fused leg (FD 16-velocity 4096^2, the temporally blocked RK3 step against the
@@ -543,22 +544,26 @@ SERVED_SIDES = (64, 128, 256, 512, 1024, 2048, 4096)
 SERVED_STEPS = (1000, 20000)
 
 
-def lattice_rates(torch, sides, steps=8):
-    """Single-lattice FP32 rates (lattice updates per second) of the served
-    instance kinds, CS (in place) and FD 16-velocity, per side: a few steps
-    of one lattice alone after one untimed step."""
+def lattice_rates(torch, sides, steps=8, prec="fp32"):
+    """Single-lattice rates (lattice updates per second) of the served
+    instance kinds, CS and FD 16-velocity, per side: a few steps of one
+    lattice alone after one untimed step. FP32: CS in place, as served;
+    FP64: the plain form (two-buffer CS), fewer steps for the large FD
+    lattices, whose FP64 step takes up to 0.2 s."""
     import paper_1904_02471_gb300 as pkg
     rates = {}
     for model in ("cs", "fd"):
         for n in sides:
             d = {"model": model, "n": n, "tau_star": 0.8}
-            s = _instance_spec(pkg, d, "fp32")
-            with pkg.Lattice(model, s.q_per_axis, n, n, s.tau, dt=s.dt, precision="fp32",
-                             storage="inplace" if model == "cs" else "ab") as L:
+            s = _instance_spec(pkg, d, prec)
+            with pkg.Lattice(model, s.q_per_axis, n, n, s.tau, dt=s.dt, precision=prec,
+                             storage="inplace" if (model == "cs" and prec == "fp32") else "ab") as L:
                 L.init(*_fields(d))
                 L.step(1)
                 L.sync()
                 k = steps if model == "fd" and n > 512 else 64 * steps
+                if prec == "fp64" and model == "fd":
+                    k = 2 if n >= 2048 else (steps if n >= 256 else 8 * steps)
                 t0 = time.perf_counter()
                 L.step(k)
                 L.sync()
@@ -659,6 +664,17 @@ def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERV
                  "rows": [[r["model"], r["n"], r["steps"], round(r["arrival"], 2), round(x["t_done"] - x["t_submit"], 3)]
                           for r, x in zip(reqs, res)]},
     }
+    # the plain FP64 form on the same request list: each run alone, one after
+    # another, at its measured single-lattice FP64 rate
+    r64 = lattice_rates(torch, sides, prec="fp64")
+    t64 = sum(r["n"] ** 2 * r["steps"] / r64[(r["model"], r["n"])] for r in reqs)
+    out["fp64_one_at_a_time"] = {
+        "mlups": round(work / t64 / 1e6, 2), "s": round(t64, 1),
+        "how": "the same request list in FP64, each run alone and one after another: sum of side^2 x steps over "
+               "the sum of each run's time at its measured single-lattice FP64 rate (CS two buffers, FD 16-velocity; "
+               "a few timed steps per kind and side)",
+        "single_lattice_mlups": {f"{m}{n}": round(v / 1e6, 2) for (m, n), v in r64.items()}}
+    out["speedup_vs_fp64_one_at_a_time"] = round(out["aggregate_mlups"] / out["fp64_one_at_a_time"]["mlups"], 1)
     if vel:
         out["fp32_vs_fp64"] = _error_summary(
             vel, rdec, lnd, f"every run of side <= {max_err_side} ({len(vel)} of {n_req}), its kept final fields "
