@@ -571,6 +571,12 @@ def lattice_rates(torch, sides, steps=8, prec="fp32"):
     return rates
 
 
+def alone_seconds(reqs, rates):
+    """Each run's time alone: side^2 x steps at its kind's single-lattice rate
+    (lattice updates per second, keyed by (model, side))."""
+    return [r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in reqs]
+
+
 def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERVED_STEPS, budget_gb=128,
                chunk=128, max_err_side=256, rates=None):
     """Served stream: Poisson arrivals of CS / FD 16-velocity Taylor-Green runs
@@ -586,7 +592,7 @@ def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERV
     if rates is None:
         rates = lattice_rates(torch, sides)
     probe = wl.served_stream(n_req, seed, rate_per_s=1.0, sides=sides, steps=steps)
-    service = sum(r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in probe) / n_req
+    service = sum(alone_seconds(probe, rates)) / n_req
     rate = load / service
     reqs = wl.served_stream(n_req, seed, rate_per_s=rate, sides=sides, steps=steps)
     work = sum(r["n"] ** 2 * r["steps"] for r in reqs)
@@ -641,7 +647,7 @@ def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERV
         B.close()
     p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
     # slowdown: latency over the run's time alone at its measured single-lattice rate
-    alone = [r["n"] ** 2 * r["steps"] / rates[(r["model"], r["n"])] for r in reqs]
+    alone = alone_seconds(reqs, rates)
     late = [x["t_done"] - x["t_submit"] for x in res]
     slow = sorted(l / a for l, a in zip(late, alone))
     worst = max(range(n_req), key=lambda i: late[i])
@@ -667,7 +673,7 @@ def run_served(torch, n_req=48, load=1.0, seed=0, sides=SERVED_SIDES, steps=SERV
     # the plain FP64 form on the same request list: each run alone, one after
     # another, at its measured single-lattice FP64 rate
     r64 = lattice_rates(torch, sides, prec="fp64")
-    t64 = sum(r["n"] ** 2 * r["steps"] / r64[(r["model"], r["n"])] for r in reqs)
+    t64 = sum(alone_seconds(reqs, r64))
     out["fp64_one_at_a_time"] = {
         "mlups": round(work / t64 / 1e6, 2), "s": round(t64, 1),
         "how": "the same request list in FP64, each run alone and one after another: sum of side^2 x steps over "
