@@ -472,6 +472,14 @@ void lbm_server_destroy(lbm_server* s);
  * the same way. LBM_EINVAL for n < 0, chunk_steps < 1, a null array with
  * n > 0 or a negative left[i]; a bad spec returns what lbm_create returns. */
 int lbm_server_plan_round(const lbm_spec* specs, const int64_t* left, int n, int chunk_steps, int64_t* steps);
+/* Device bytes a lattice of this spec holds (its state buffers and the
+ * per-lattice observables scratch): the footprint the server admits runs by
+ * against its HBM budget, and what lbm_create allocates for the state.
+ * Host only (no device work). Two-buffer CS keeps two copies of the 9
+ * planes, in-place CS one; FD three copies of the Q^2 planes (RK3: f^n and
+ * two stage buffers; IMEX: f^n, Z and P) and two with LBM_TS_RK3_FUSED.
+ * A bad spec returns what lbm_create returns; *bytes is then not written. */
+int lbm_footprint(const lbm_spec* spec, size_t* bytes);
 
 /* Test injection of a device-side wait that runs out (no counterpart in the
  * paper; failure detection of the library itself). The CS bulk-copy kernel

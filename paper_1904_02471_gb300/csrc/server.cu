@@ -526,6 +526,18 @@ int lbm_server_plan_round(const lbm_spec* specs, const int64_t* left, int n, int
     }
 }
 
+int lbm_footprint(const lbm_spec* spec, size_t* bytes) {
+    if (!spec || !bytes) {
+        lbm::set_error("lbm_footprint needs a spec and an output");
+        return LBM_EINVAL;
+    }
+    lbm_spec norm;
+    const int rc = lbm::Engine::validate(spec, &norm);
+    if (rc) return rc;
+    *bytes = lbm::Engine::footprint(norm);
+    return LBM_OK;
+}
+
 int lbm_server_inject_wait_timeout(lbm_server* s, int microseconds) {
     if (!s || microseconds < 0 || microseconds > 1000000) {
         lbm::set_error("wait-timeout injection takes 0 (off) to 1e6 microseconds");

@@ -153,6 +153,7 @@ _SIGS = [
                               ctypes.POINTER(_sz)]),
     ("lbm_server_destroy", None, [_P]),
     ("lbm_server_plan_round", _i, [ctypes.POINTER(lbm_spec), ctypes.POINTER(_i64), _i, _i, ctypes.POINTER(_i64)]),
+    ("lbm_footprint", _i, [ctypes.POINTER(lbm_spec), ctypes.POINTER(ctypes.c_size_t)]),
     ("lbm_observables_noalloc", _i, [_i, _i, _i, _i, _i, _P, _i64, ctypes.c_int32, ctypes.c_int32, _d, _i, _P, _P,
                                      _d, _i64, _d, _P, _P]),
 ]
@@ -560,6 +561,13 @@ def plan_round(specs, left, chunk_steps):
     out = (_i64 * max(n, 1))()
     check(lib().lbm_server_plan_round(arr, lft, n, int(chunk_steps), out), "lbm_server_plan_round")
     return [int(out[i]) for i in range(n)]
+
+
+def footprint(spec):
+    """Device bytes a lattice of this spec holds (lbm_footprint)."""
+    out = ctypes.c_size_t()
+    check(lib().lbm_footprint(ctypes.byref(spec), ctypes.byref(out)), "lbm_footprint")
+    return out.value
 
 
 class Server:

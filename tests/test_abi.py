@@ -269,3 +269,31 @@ def test_scheme_validation(kw, code):
     with pytest.raises(lbm.LbmError) as ei:
         pkg.spec_from_nu("fd", 4, 32, 32, 1e-4, "fd", dt=1e-3, precision="fp32")
     assert ei.value.code == lbm.LBM_ESTIFF
+
+
+def test_footprint_follows_the_state_buffers():
+    """Device bytes per lattice (host only): in-place CS holds one copy of the
+    9 planes against two, the temporally blocked FD step two copies of the
+    Q^2 planes against three, FP64 twice the FP32 bytes; rows are padded to
+    a pitch of 32 (plus 8 nodes of slack) and each lattice has 32 KiB of
+    observables scratch."""
+    from paper_1904_02471_gb300 import lbm
+    scratch = 8 * 4 * 1024
+
+    def fp(*a, **kw):
+        return lbm.footprint(pkg.make_spec(*a, **kw)) - scratch
+
+    n = 1000
+    plane = ((n + 8 + 31) // 32 * 32) * n           # pitch 1024
+    tail = 1024                                      # spare elements per buffer
+    assert fp("cs", 3, n, n, 0.6, 0.0, 0.0, "fp32") == 2 * (9 * plane + tail) * 4
+    assert fp("cs", 3, n, n, 0.6, 0.0, 0.0, "fp32", storage="inplace") == (9 * plane + tail) * 4
+    assert fp("cs", 3, n, n, 0.6, 0.0, 0.0, "fp64") == 2 * (9 * plane + tail) * 8
+    tau = dt = 1e-4
+    assert fp("fd", 4, n, n, tau, dt, 0.0, "fp32") == 3 * (16 * plane + tail) * 4
+    assert fp("fd", 4, n, n, tau, dt, 0.0, "fp32", scheme="imex") == 3 * (16 * plane + tail) * 4
+    assert fp("fd", 4, n, n, tau, dt, 0.0, "fp32", scheme="rk3_fused") == 2 * (16 * plane + tail) * 4
+    assert fp("fd", 5, n, n, tau, dt, 0.0, "fp64", scheme="rk3_fused") == 2 * (25 * plane + tail) * 8
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.footprint(pkg.make_spec("fd", 4, n, n, 1e-4, 2e-4, 0.0, "fp32"))   # dt > tau
+    assert e.value.code == lbm.LBM_ESTIFF
