@@ -29,6 +29,8 @@
 // formed once per stage and node, before the groups. Stage 2 updates f^(1)
 // into f^(2) in place: a group's new values are held in registers until every
 // thread has read the group's old neighbour values, then written.
+#include <atomic>
+
 #include "fd_common.cuh"
 #include "kernels.h"
 #include "ptx.cuh"
@@ -489,10 +491,12 @@ int fd_fused_threads(int precision) { return precision == LBM_FP64 ? 256 : 512; 
 // Variants that do not fit the device (or tile shapes without a fused
 // kernel) are refused.
 static cudaError_t fused_prepare(int precision, int tile, int q1) {
-    static int state[2][FD_NTILES][3] = {};   // 0 unknown, 1 ready, 2 unavailable
+    // 0 unknown, 1 ready, 2 unavailable; atomic: the two lanes of a server
+    // may prepare the same variant at once (both then make the same calls)
+    static std::atomic<int> state[2][FD_NTILES][3] = {};
     if (tile < 0 || tile >= FD_NTILES || q1 < 3 || q1 > 5) return cudaErrorInvalidValue;
     const int p = precision == LBM_FP64 ? 0 : 1;
-    int& st = state[p][tile][q1 - 3];
+    std::atomic<int>& st = state[p][tile][q1 - 3];
     if (st == 1) return cudaSuccess;
     if (st == 2) return cudaErrorInvalidConfiguration;
     const int ty = fused_ty(tile);
